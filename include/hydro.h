@@ -1,0 +1,189 @@
+/*
+ * hydro.h -- C ABI of libhydro: the directionally split second-order Godunov
+ * scheme of the HYDRO mini-application (§1), advanced on one GB300 GPU.
+ *
+ * The library owns a context holding one or more independent 2D grids of
+ * conserved variables U = (rho, rho*u, rho*v, E) (the "2D grid buffer for
+ * conservative variables" of Fig. 5).  A time step of every grid is the one
+ * §1 and Fig. 5 describe: a 1D Godunov sweep along x over every row, then
+ * one along y over every column (the order alternates from step to step),
+ * each sweep computing primitive variables, solving a Riemann problem at
+ * every cell interface and applying the interface fluxes.  The update of a
+ * cell in a sweep reads the cells i-2..i+2 of its line (Figs. 1-2).
+ *
+ * Conventions shared by every entry point
+ *   - Host-side state arrays are FP64, SoA planes [4][ny][nx] in the order
+ *     (rho, rho*u, rho*v, E), x fastest, interior cells only (no ghosts).
+ *   - Pointers marked "host or device" are device pointers when the call's
+ *     on_device argument is non-zero (e.g. a CUDA tensor's data pointer in
+ *     the same CUDA context), host pointers otherwise.  Host buffers may be
+ *     pageable; page-locked buffers copy faster.
+ *   - The caller owns every buffer it passes; the library copies in and out
+ *     and keeps no pointer to a caller buffer after a call returns.
+ *   - Every call returns a hydro_status; no exception or signal crosses the
+ *     ABI.  On failure hydro_last_error(ctx) gives a one-line message.
+ *   - A context is used by one host thread at a time.
+ *   - Work is enqueued on the context's CUDA stream; calls that return data
+ *     to the host synchronise that stream.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hydro_ctx hydro_ctx; /* opaque; owns all device memory */
+
+typedef enum {
+    HYDRO_OK = 0,
+    HYDRO_EINVAL = 1,    /* bad argument: null pointer, size, index, bc, ... */
+    HYDRO_ENOMEM = 2,    /* device or host allocation failed */
+    HYDRO_ECUDA = 3,     /* a CUDA runtime call failed (no device, launch error) */
+    HYDRO_ENEGATIVE = 4, /* a non-positive or NaN density or energy appeared */
+    HYDRO_ETIMEOUT = 5   /* a bounded device-side wait gave up (reserved) */
+} hydro_status;
+
+/* Boundary conditions of one side (§1/Fig. 5 "apply boundary conditions";
+ * 2 ghost cells per side, the stencil width of Figs. 1-2):
+ *   REFLECT      mirror image, momentum normal to the wall negated
+ *   TRANSMISSIVE mirror image without sign change (zero gradient)
+ *   PERIODIC     wrap-around; both sides of an axis must be periodic */
+enum { HYDRO_BC_REFLECT = 0, HYDRO_BC_TRANSMISSIVE = 1, HYDRO_BC_PERIODIC = 2 };
+
+enum { HYDRO_PREC_FP32 = 32, HYDRO_PREC_FP64 = 64 };
+
+/* One grid: nx * ny interior cells (each >= 2), square cells of side h > 0,
+ * boundary conditions bc[] = {x low, x high, y low, y high}. */
+typedef struct {
+    int nx, ny;
+    double h;
+    int bc[4];
+} hydro_grid;
+
+/* Scheme and run parameters.
+ *   precision      HYDRO_PREC_FP64: state and arithmetic in FP64.
+ *                  HYDRO_PREC_FP32: state and arithmetic in FP32; a Riemann
+ *                  problem near vacuum is solved again in FP64; dt and the
+ *                  conservation sums are FP64.
+ *   gamma          ratio of specific heats (> 1)
+ *   cfl            Courant number C of dt = C h / max(max(|u|,|v|) + c)
+ *   niter_riemann  maximum Newton iterations of the Riemann solver (the
+ *                  iteration stops earlier once it has converged)
+ *   rho_floor      density floor (> 0)
+ *   c_floor        sound-speed floor: p >= rho c_floor^2 / gamma (> 0)
+ *   ngrids, grids  the grids this context advances together (>= 1)
+ *   cuda_stream    a cudaStream_t to enqueue on, or NULL for a stream the
+ *                  context creates and owns */
+typedef struct {
+    int precision;
+    double gamma, cfl;
+    int niter_riemann;
+    double rho_floor, c_floor;
+    int ngrids;
+    const hydro_grid *grids;
+    void *cuda_stream;
+} hydro_params;
+
+/* Launch shape of the sweep kernels (all fields 0 = library default).
+ *   tile_len      cells per tile along the sweep line (>= 4)
+ *   ctas_per_sm   resident CTAs per SM of the persistent sweep launch
+ *   graph_steps   steps captured per CUDA graph (even, 0 = no graph)
+ * Results are bit-identical for every admissible setting. */
+typedef struct {
+    int tile_len;
+    int ctas_per_sm;
+    int graph_steps;
+} hydro_tuning;
+
+/* Counters kept on the device since hydro_init (hydro_stats()).
+ *   steps          completed steps
+ *   riemann_fp64   FP32 contexts: interface solves redone in FP64 near vacuum
+ *   status_flags   bit 0: non-positive/NaN density, bit 1: non-positive/NaN
+ *                  energy (sticky until hydro_set_state) */
+typedef struct {
+    long long steps;
+    long long riemann_fp64;
+    unsigned int status_flags;
+} hydro_stats;
+
+/* Create a context: validates params, allocates two state buffers (the step
+ * ping-pongs between them) for all grids plus the per-grid dt/time records,
+ * and builds the tile work-lists.  The state is zero until hydro_set_state.
+ * Returns HYDRO_EINVAL for invalid params, HYDRO_ECUDA when no usable GPU is
+ * present, HYDRO_ENOMEM when allocation fails; *out is NULL on failure. */
+hydro_status hydro_init(const hydro_params *params, hydro_ctx **out);
+
+/* Release the context and all its device memory.  NULL is a no-op. */
+void hydro_destroy(hydro_ctx *ctx);
+
+/* Choose the launch shape (see hydro_tuning).  HYDRO_EINVAL for values out
+ * of range.  Applies to later hydro_step calls. */
+hydro_status hydro_set_tuning(hydro_ctx *ctx, const hydro_tuning *tuning);
+
+/* Load the state of grid `grid` from U (host or device, [4][ny][nx] FP64).
+ * Resets the grid's time to 0 and the context's step counter (which sets the
+ * sweep order) to 0, clears the status flags, and computes the CFL wave
+ * speed of the new state.  FP32 contexts round U to FP32. */
+hydro_status hydro_set_state(hydro_ctx *ctx, int grid, const double *U, int on_device);
+
+/* Copy the current state of grid `grid` into U_out (host or device,
+ * [4][ny][nx] FP64).  Synchronises the context's stream. */
+hydro_status hydro_get_state(hydro_ctx *ctx, int grid, double *U_out, int on_device);
+
+/* Advance every grid by nsteps steps (§1, Fig. 5).  Step k (counted from the
+ * last hydro_set_state) sweeps x then y when k is even and y then x when k
+ * is odd; both sweeps use the step's dt.  dt is each grid's CFL step of the
+ * state at the start of the step, unless dt_override (host, nsteps * ngrids
+ * values, step-major: dt_override[s * ngrids + g]) is given.  Returns
+ * HYDRO_ENEGATIVE when a non-positive or NaN density or energy appeared (the
+ * state is then the one after the last step; the context stays usable).
+ * Synchronises the context's stream once at the end to read the status. */
+hydro_status hydro_step(hydro_ctx *ctx, int nsteps, const double *dt_override);
+
+/* hydro_step that also returns the dt each grid used at each step in
+ * dt_used (host, nsteps * ngrids values, step-major) when non-NULL. */
+hydro_status hydro_step_dt(hydro_ctx *ctx, int nsteps, const double *dt_override,
+                           double *dt_used);
+
+/* hydro_step without graph capture that also times every kernel launch
+ * with CUDA events on the context's stream: kernel_ms (host, 3 * nsteps
+ * values) receives, per step, the durations of the dt prologue, the first
+ * sweep and the second sweep in milliseconds.  Same results as hydro_step. */
+hydro_status hydro_step_profiled(hydro_ctx *ctx, int nsteps, double *kernel_ms);
+
+/* CFL time step dt = C h / max over cells of (max(|u|,|v|) + c) of the
+ * current state of grid `grid` (FP64). */
+hydro_status hydro_cfl_dt(hydro_ctx *ctx, int grid, double *dt_out);
+
+/* Simulated time of grid `grid` (sum of the dt it was advanced by). */
+hydro_status hydro_get_time(hydro_ctx *ctx, int grid, double *t_out);
+
+/* Step counter since the last hydro_set_state (its parity sets the sweep
+ * order of the next step).  hydro_set_step restores it when a run resumes
+ * from a checkpoint (hydro_get_state + hydro_get_step + hydro_get_time);
+ * step >= 0. */
+hydro_status hydro_get_step(hydro_ctx *ctx, long long *step_out);
+hydro_status hydro_set_step(hydro_ctx *ctx, long long step);
+
+/* Set the simulated time of grid `grid` (checkpoint restore). */
+hydro_status hydro_set_time(hydro_ctx *ctx, int grid, double t);
+
+/* Domain totals h^2 * sum over cells of each conserved variable of grid
+ * `grid`, in FP64 and in a fixed summation order (bit-reproducible). */
+hydro_status hydro_conservation(hydro_ctx *ctx, int grid, double sums[4]);
+
+/* Device counters (see hydro_stats). */
+hydro_status hydro_get_stats(hydro_ctx *ctx, hydro_stats *out);
+
+/* Message of the last failure on this context ("" if none); valid until the
+ * next call on ctx.  With ctx == NULL: the last hydro_init failure. */
+const char *hydro_last_error(const hydro_ctx *ctx);
+
+/* Library version, "major.minor.patch". */
+const char *hydro_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYDRO_H */

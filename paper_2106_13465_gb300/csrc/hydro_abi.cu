@@ -1,0 +1,618 @@
+// hydro_abi.cu -- the C ABI of include/hydro.h: context and HBM layout, tile
+// work-lists, the step driver (§1, Fig. 5: per step a dt, then a sweep along
+// each direction, the order alternating), CUDA-graph capture of the step
+// loop, state transfer and diagnostics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hydro.h"
+#include "kernels.h"
+
+using namespace hydro;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+constexpr int kDefaultTileLen = 64;
+constexpr int kDefaultGraphSteps = 20;
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+template <class T>
+Consts<T> make_consts(const hydro_params& p, double tol) {
+    const double g = p.gamma;
+    Consts<T> K;
+    K.gamma = (T)g;
+    K.gm1 = (T)(g - 1.0);
+    K.inv_gm1 = (T)(1.0 / (g - 1.0));
+    K.z = (T)((g - 1.0) / (2.0 * g));
+    K.zs = (T)((g + 1.0) / (2.0 * g));
+    K.G3 = (T)(2.0 * g / (g - 1.0));
+    K.G4 = (T)(2.0 / (g - 1.0));
+    K.G5 = (T)(2.0 / (g + 1.0));
+    K.G6 = (T)((g - 1.0) / (g + 1.0));
+    K.G7 = (T)((g - 1.0) / 2.0);
+    K.inv_g = (T)(1.0 / g);
+    K.rho_floor = (T)p.rho_floor;
+    K.cf2g = (T)(p.c_floor * p.c_floor / g);
+    K.pmin = (T)(p.rho_floor * (p.c_floor * p.c_floor / g));
+    K.tol = (T)tol;
+    K.niter = p.niter_riemann;
+    return K;
+}
+
+}  // namespace
+
+struct hydro_ctx {
+    int prec = 64;
+    size_t esz = 8;
+    double cfl = 0.8;
+    Consts<double> Kd{};
+    Consts<float> Kf{};
+    std::vector<hydro_grid> grids;
+    std::vector<GridDesc> gd;
+    int device = 0;
+    int nsm = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t capture_stream = nullptr;
+    void* buf[2] = {nullptr, nullptr};
+    size_t buf_elems = 0;
+    GridDesc* d_grids = nullptr;
+    Tile* d_tiles[2] = {nullptr, nullptr};
+    int ntiles[2] = {0, 0};
+    GridRun* d_run = nullptr;
+    DevCounters* d_ctr = nullptr;
+    double* d_stage = nullptr;  // FP64 [4][ny][nx] staging (FP32 contexts)
+    double* d_rows = nullptr;   // conservation row sums [4][max ny]
+    double* d_out4 = nullptr;
+    double* d_dt_ovr = nullptr;
+    size_t dt_ovr_cap = 0;
+    double* d_dt_log = nullptr;
+    size_t dt_log_cap = 0;
+    hydro_tuning tuning{kDefaultTileLen, 0, kDefaultGraphSteps};
+    int ctas[2] = {0, 0};       // CTAs per sweep launch (x, y)
+    long long step = 0;         // steps since the last hydro_set_state
+    cudaGraphExec_t gexec = nullptr;
+    int gexec_steps = 0;
+    std::string err;
+};
+
+namespace {
+
+hydro_status fail(hydro_ctx* c, hydro_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_init_error = msg;
+    return st;
+}
+
+hydro_status fail_cuda(hydro_ctx* c, const char* what, cudaError_t e) {
+    return fail(c, HYDRO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define HCK(ctx, call)                                                  \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return fail_cuda((ctx), #call, e_);      \
+    } while (0)
+
+bool valid_bc(const int bc[4]) {
+    for (int k = 0; k < 4; ++k)
+        if (bc[k] < HYDRO_BC_REFLECT || bc[k] > HYDRO_BC_PERIODIC) return false;
+    if ((bc[0] == HYDRO_BC_PERIODIC) != (bc[1] == HYDRO_BC_PERIODIC)) return false;
+    if ((bc[2] == HYDRO_BC_PERIODIC) != (bc[3] == HYDRO_BC_PERIODIC)) return false;
+    return true;
+}
+
+hydro_status validate_params(const hydro_params* p) {
+    if (!p) return fail(nullptr, HYDRO_EINVAL, "params is NULL");
+    if (p->precision != HYDRO_PREC_FP32 && p->precision != HYDRO_PREC_FP64)
+        return fail(nullptr, HYDRO_EINVAL, "precision must be 32 or 64");
+    if (!(p->gamma > 1.0) || !std::isfinite(p->gamma))
+        return fail(nullptr, HYDRO_EINVAL, "gamma must be finite and > 1");
+    if (!(p->cfl > 0.0) || !std::isfinite(p->cfl))
+        return fail(nullptr, HYDRO_EINVAL, "cfl must be finite and > 0");
+    if (p->niter_riemann < 0 || p->niter_riemann > 1000)
+        return fail(nullptr, HYDRO_EINVAL, "niter_riemann must be in [0, 1000]");
+    if (!(p->rho_floor > 0.0) || !(p->c_floor > 0.0))
+        return fail(nullptr, HYDRO_EINVAL, "rho_floor and c_floor must be > 0");
+    if (p->ngrids < 1 || !p->grids)
+        return fail(nullptr, HYDRO_EINVAL, "need ngrids >= 1 and a grids array");
+    for (int g = 0; g < p->ngrids; ++g) {
+        const hydro_grid& G = p->grids[g];
+        char buf[160];
+        if (G.nx < 2 || G.ny < 2 || G.nx > (1 << 24) || G.ny > (1 << 24)) {
+            snprintf(buf, sizeof buf, "grid %d: nx, ny must be in [2, 2^24] (got %d x %d)", g, G.nx, G.ny);
+            return fail(nullptr, HYDRO_EINVAL, buf);
+        }
+        if (!(G.h > 0.0) || !std::isfinite(G.h)) {
+            snprintf(buf, sizeof buf, "grid %d: h must be finite and > 0", g);
+            return fail(nullptr, HYDRO_EINVAL, buf);
+        }
+        if (!valid_bc(G.bc)) {
+            snprintf(buf, sizeof buf, "grid %d: bad boundary conditions (periodic must pair)", g);
+            return fail(nullptr, HYDRO_EINVAL, buf);
+        }
+    }
+    return HYDRO_OK;
+}
+
+// Tile work-lists: for each grid, lines in groups of 32 (one per lane),
+// cells along the line in segments of tile_len.
+void build_tiles(const std::vector<GridDesc>& gd, int tile_len, std::vector<Tile> out[2]) {
+    for (int d = 0; d < 2; ++d) {
+        out[d].clear();
+        for (int g = 0; g < (int)gd.size(); ++g) {
+            const int nlines = d == DIR_X ? gd[g].ny : gd[g].nx;
+            const int n = d == DIR_X ? gd[g].nx : gd[g].ny;
+            for (int l0 = 0; l0 < nlines; l0 += kWarpLines)
+                for (int c0 = 0; c0 < n; c0 += tile_len)
+                    out[d].push_back(Tile{g, l0, c0, std::min(tile_len, n - c0)});
+        }
+    }
+}
+
+hydro_status upload_tiles(hydro_ctx* c) {
+    std::vector<Tile> t[2];
+    build_tiles(c->gd, c->tuning.tile_len, t);
+    for (int d = 0; d < 2; ++d) {
+        if (c->d_tiles[d]) cudaFree(c->d_tiles[d]);
+        c->d_tiles[d] = nullptr;
+        HCK(c, cudaMalloc(&c->d_tiles[d], sizeof(Tile) * t[d].size()));
+        HCK(c, cudaMemcpy(c->d_tiles[d], t[d].data(), sizeof(Tile) * t[d].size(),
+                          cudaMemcpyHostToDevice));
+        c->ntiles[d] = (int)t[d].size();
+        int per_sm = c->tuning.ctas_per_sm;
+        if (per_sm <= 0)
+            per_sm = c->prec == 64 ? sweep_ctas_per_sm<double>(d) : sweep_ctas_per_sm<float>(d);
+        if (per_sm <= 0) per_sm = 1;
+        const int warps_per_cta = kSweepThreads / 32;
+        const int need = (c->ntiles[d] + warps_per_cta - 1) / warps_per_cta;
+        c->ctas[d] = std::max(1, std::min(need, c->nsm * per_sm));
+    }
+    return HYDRO_OK;
+}
+
+void drop_graph(hydro_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gexec_steps = 0;
+}
+
+template <class T>
+SweepArgs<T> sweep_args(hydro_ctx* c, int which, const Consts<T>& K) {
+    SweepArgs<T> a;
+    a.src = (const T*)c->buf[which];
+    a.dst = (T*)c->buf[which ^ 1];
+    a.grids = c->d_grids;
+    a.tiles = nullptr;
+    a.ntiles = 0;
+    a.which = which;
+    a.run = c->d_run;
+    a.ctr = c->d_ctr;
+    a.K = K;
+    a.Kd = c->Kd;
+    return a;
+}
+
+// Enqueue one step of parity `parity` on stream s; ev (optional, 4 events)
+// brackets the three launches for timing.
+template <class T>
+cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* log,
+                           cudaStream_t s, const Consts<T>& K, cudaEvent_t* ev) {
+    cudaError_t e;
+    if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
+    e = launch_step_prologue(c->d_run, c->d_grids, (int)c->gd.size(), c->d_ctr, ovr, c->cfl, log, s);
+    if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
+    const int first = parity == 0 ? DIR_X : DIR_Y;
+    for (int which = 0; which < 2; ++which) {
+        const int dir = which == 0 ? first : (first ^ 1);
+        SweepArgs<T> a = sweep_args<T>(c, which, K);
+        a.tiles = c->d_tiles[dir];
+        a.ntiles = c->ntiles[dir];
+        e = launch_sweep<T>(dir, a, c->ctas[dir], s);
+        if (e != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecord(ev[2 + which], s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_step(hydro_ctx* c, int parity, const double* ovr, double* log, cudaStream_t s,
+                         cudaEvent_t* ev = nullptr) {
+    if (c->prec == 64) return enqueue_step_t<double>(c, parity, ovr, log, s, c->Kd, ev);
+    return enqueue_step_t<float>(c, parity, ovr, log, s, c->Kf, ev);
+}
+
+hydro_status ensure_graph(hydro_ctx* c, int steps) {
+    if (c->gexec && c->gexec_steps == steps) return HYDRO_OK;
+    drop_graph(c);
+    cudaGraph_t graph = nullptr;
+    HCK(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < steps && e == cudaSuccess; ++k)
+        e = enqueue_step(c, k & 1, nullptr, nullptr, c->capture_stream);
+    cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail_cuda(c, "sweep launch during graph capture", e);
+    }
+    if (e2 != cudaSuccess) return fail_cuda(c, "cudaStreamEndCapture", e2);
+    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return fail_cuda(c, "cudaGraphInstantiate", e);
+    }
+    c->gexec_steps = steps;
+    return HYDRO_OK;
+}
+
+hydro_status check_grid(hydro_ctx* c, int grid) {
+    if (!c) return fail(nullptr, HYDRO_EINVAL, "ctx is NULL");
+    if (grid < 0 || grid >= (int)c->gd.size()) return fail(c, HYDRO_EINVAL, "grid index out of range");
+    return HYDRO_OK;
+}
+
+template <class T>
+T* state_ptr(hydro_ctx* c) { return (T*)c->buf[0]; }
+
+}  // namespace
+
+extern "C" {
+
+hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
+    if (!out) return fail(nullptr, HYDRO_EINVAL, "out is NULL");
+    *out = nullptr;
+    hydro_status st = validate_params(params);
+    if (st != HYDRO_OK) return st;
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1)
+        return fail(nullptr, HYDRO_ECUDA,
+                    std::string("no CUDA device: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "count 0"));
+
+    hydro_ctx* c = new (std::nothrow) hydro_ctx();
+    if (!c) return fail(nullptr, HYDRO_ENOMEM, "host allocation failed");
+    auto bail = [&](hydro_status s) {
+        g_init_error = c->err;
+        hydro_destroy(c);
+        return s;
+    };
+
+    c->prec = params->precision;
+    c->esz = c->prec == 64 ? 8 : 4;
+    c->cfl = params->cfl;
+    c->Kd = make_consts<double>(*params, 1e-12);
+    c->Kf = make_consts<float>(*params, 1e-6);
+    c->grids.assign(params->grids, params->grids + params->ngrids);
+    cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->nsm <= 0) c->nsm = 1;
+
+    // HBM layout (see kernels.h)
+    long long off = 0, max_cells = 0, max_ny = 0;
+    const long long align_elems = 256 / (long long)c->esz;
+    for (const hydro_grid& G : c->grids) {
+        GridDesc d{};
+        d.nx = G.nx;
+        d.ny = G.ny;
+        d.pitch = (int)round_up(G.nx, 32);
+        d.plane = (long long)d.pitch * G.ny;
+        d.off = off;
+        for (int k = 0; k < 4; ++k) d.bc[k] = G.bc[k];
+        d.h = G.h;
+        off = round_up(off + 4 * d.plane, align_elems);
+        max_cells = std::max(max_cells, (long long)G.nx * G.ny);
+        max_ny = std::max(max_ny, (long long)G.ny);
+        c->gd.push_back(d);
+    }
+    c->buf_elems = (size_t)off;
+
+    if (params->cuda_stream) {
+        c->stream = (cudaStream_t)params->cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { fail_cuda(c, "cudaStreamCreate", e); return bail(HYDRO_ECUDA); }
+        c->own_stream = true;
+    }
+    e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { fail_cuda(c, "cudaStreamCreate", e); return bail(HYDRO_ECUDA); }
+
+    auto alloc = [&](void** p, size_t bytes, const char* what) -> hydro_status {
+        cudaError_t ea = cudaMalloc(p, bytes);
+        if (ea != cudaSuccess) {
+            cudaGetLastError();
+            char buf[200];
+            snprintf(buf, sizeof buf, "cudaMalloc(%s, %zu bytes): %s", what, bytes, cudaGetErrorString(ea));
+            return fail(c, ea == cudaErrorMemoryAllocation ? HYDRO_ENOMEM : HYDRO_ECUDA, buf);
+        }
+        return HYDRO_OK;
+    };
+    for (int b = 0; b < 2; ++b)
+        if ((st = alloc(&c->buf[b], c->buf_elems * c->esz, "state buffer")) != HYDRO_OK) return bail(st);
+    if ((st = alloc((void**)&c->d_grids, sizeof(GridDesc) * c->gd.size(), "grids")) != HYDRO_OK) return bail(st);
+    if ((st = alloc((void**)&c->d_run, sizeof(GridRun) * c->gd.size(), "run records")) != HYDRO_OK) return bail(st);
+    if ((st = alloc((void**)&c->d_ctr, sizeof(DevCounters), "counters")) != HYDRO_OK) return bail(st);
+    if ((st = alloc((void**)&c->d_rows, sizeof(double) * 4 * max_ny, "row sums")) != HYDRO_OK) return bail(st);
+    if ((st = alloc((void**)&c->d_out4, sizeof(double) * 4, "sums")) != HYDRO_OK) return bail(st);
+    if (c->prec == 32 &&
+        (st = alloc((void**)&c->d_stage, sizeof(double) * 4 * max_cells, "staging")) != HYDRO_OK)
+        return bail(st);
+
+    e = cudaMemcpy(c->d_grids, c->gd.data(), sizeof(GridDesc) * c->gd.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->d_run, 0, sizeof(GridRun) * c->gd.size());
+    if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaMemset(c->buf[0], 0, c->buf_elems * c->esz);
+    if (e == cudaSuccess) e = cudaMemset(c->buf[1], 0, c->buf_elems * c->esz);
+    if (e != cudaSuccess) { fail_cuda(c, "context set-up", e); return bail(HYDRO_ECUDA); }
+    if ((st = upload_tiles(c)) != HYDRO_OK) return bail(st);
+
+    *out = c;
+    return HYDRO_OK;
+}
+
+void hydro_destroy(hydro_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    for (int b = 0; b < 2; ++b) cudaFree(c->buf[b]);
+    for (int d = 0; d < 2; ++d) cudaFree(c->d_tiles[d]);
+    cudaFree(c->d_grids);
+    cudaFree(c->d_run);
+    cudaFree(c->d_ctr);
+    cudaFree(c->d_stage);
+    cudaFree(c->d_rows);
+    cudaFree(c->d_out4);
+    cudaFree(c->d_dt_ovr);
+    cudaFree(c->d_dt_log);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+hydro_status hydro_set_tuning(hydro_ctx* c, const hydro_tuning* t) {
+    if (!c || !t) return fail(c, HYDRO_EINVAL, "ctx or tuning is NULL");
+    hydro_tuning n = *t;
+    if (n.tile_len == 0) n.tile_len = kDefaultTileLen;
+    if (n.tile_len < 4 || n.tile_len > (1 << 24)) return fail(c, HYDRO_EINVAL, "tile_len must be in [4, 2^24]");
+    if (n.ctas_per_sm < 0 || n.ctas_per_sm > 64) return fail(c, HYDRO_EINVAL, "ctas_per_sm must be in [0, 64]");
+    if (n.graph_steps < 0 || (n.graph_steps & 1) || n.graph_steps > 1000)
+        return fail(c, HYDRO_EINVAL, "graph_steps must be even and in [0, 1000]");
+    HCK(c, cudaStreamSynchronize(c->stream));
+    c->tuning = n;
+    drop_graph(c);
+    return upload_tiles(c);
+}
+
+hydro_status hydro_set_state(hydro_ctx* c, int grid, const double* U, int on_device) {
+    hydro_status st = check_grid(c, grid);
+    if (st != HYDRO_OK) return st;
+    if (!U) return fail(c, HYDRO_EINVAL, "U is NULL");
+    const GridDesc& g = c->gd[grid];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (c->prec == 64) {
+        double* dst = state_ptr<double>(c) + g.off;
+        HCK(c, cudaMemcpy2DAsync(dst, sizeof(double) * g.pitch, U, sizeof(double) * g.nx,
+                                 sizeof(double) * g.nx, 4 * (size_t)g.ny, kind, c->stream));
+        HCK(c, launch_cfl_init<double>(state_ptr<double>(c), c->d_grids, grid, g, c->d_run, c->d_ctr,
+                                       c->Kd, c->stream));
+    } else {
+        HCK(c, cudaMemcpyAsync(c->d_stage, U, sizeof(double) * 4 * g.nx * (size_t)g.ny, kind, c->stream));
+        HCK(c, launch_pack<float>(c->d_stage, state_ptr<float>(c), g, c->stream));
+        HCK(c, launch_cfl_init<float>(state_ptr<float>(c), c->d_grids, grid, g, c->d_run, c->d_ctr,
+                                      c->Kf, c->stream));
+    }
+    // time of this grid, step counter and status flags restart
+    HCK(c, cudaMemsetAsync(&c->d_run[grid].t, 0, sizeof(double), c->stream));
+    HCK(c, cudaMemsetAsync(&c->d_ctr->status, 0, sizeof(unsigned int), c->stream));
+    HCK(c, cudaStreamSynchronize(c->stream));
+    c->step = 0;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_get_state(hydro_ctx* c, int grid, double* U, int on_device) {
+    hydro_status st = check_grid(c, grid);
+    if (st != HYDRO_OK) return st;
+    if (!U) return fail(c, HYDRO_EINVAL, "U_out is NULL");
+    const GridDesc& g = c->gd[grid];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (c->prec == 64) {
+        const double* src = state_ptr<double>(c) + g.off;
+        HCK(c, cudaMemcpy2DAsync(U, sizeof(double) * g.nx, src, sizeof(double) * g.pitch,
+                                 sizeof(double) * g.nx, 4 * (size_t)g.ny, kind, c->stream));
+    } else {
+        HCK(c, launch_unpack<float>(state_ptr<float>(c), c->d_stage, g, c->stream));
+        HCK(c, cudaMemcpyAsync(U, c->d_stage, sizeof(double) * 4 * g.nx * (size_t)g.ny, kind, c->stream));
+    }
+    HCK(c, cudaStreamSynchronize(c->stream));
+    return HYDRO_OK;
+}
+
+hydro_status hydro_step_dt(hydro_ctx* c, int nsteps, const double* dt_override, double* dt_used) {
+    if (!c) return fail(nullptr, HYDRO_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(c, HYDRO_EINVAL, "nsteps < 0");
+    if (nsteps == 0) return HYDRO_OK;
+    const size_t ng = c->gd.size();
+    const size_t nval = (size_t)nsteps * ng;
+    if (dt_override) {
+        for (size_t k = 0; k < nval; ++k)
+            if (!(dt_override[k] > 0.0) || !std::isfinite(dt_override[k]))
+                return fail(c, HYDRO_EINVAL, "dt_override values must be finite and > 0");
+        if (c->dt_ovr_cap < nval) {
+            cudaFree(c->d_dt_ovr);
+            c->d_dt_ovr = nullptr;
+            c->dt_ovr_cap = 0;
+            HCK(c, cudaMalloc(&c->d_dt_ovr, sizeof(double) * nval));
+            c->dt_ovr_cap = nval;
+        }
+        HCK(c, cudaMemcpyAsync(c->d_dt_ovr, dt_override, sizeof(double) * nval,
+                               cudaMemcpyHostToDevice, c->stream));
+    }
+    if (dt_used && c->dt_log_cap < nval) {
+        cudaFree(c->d_dt_log);
+        c->d_dt_log = nullptr;
+        c->dt_log_cap = 0;
+        HCK(c, cudaMalloc(&c->d_dt_log, sizeof(double) * nval));
+        c->dt_log_cap = nval;
+    }
+
+    int s = 0;
+    const int G = c->tuning.graph_steps;
+    if (!dt_override && !dt_used && G > 0 && nsteps >= G) {
+        if (c->step & 1) {
+            HCK(c, enqueue_step(c, 1, nullptr, nullptr, c->stream));
+            ++c->step;
+            ++s;
+        }
+        if (nsteps - s >= G) {
+            hydro_status st = ensure_graph(c, G);
+            if (st != HYDRO_OK) return st;
+            while (nsteps - s >= G) {
+                HCK(c, cudaGraphLaunch(c->gexec, c->stream));
+                c->step += G;
+                s += G;
+            }
+        }
+    }
+    for (; s < nsteps; ++s) {
+        const double* ovr = dt_override ? c->d_dt_ovr + (size_t)s * ng : nullptr;
+        double* log = dt_used ? c->d_dt_log + (size_t)s * ng : nullptr;
+        HCK(c, enqueue_step(c, (int)(c->step & 1), ovr, log, c->stream));
+        ++c->step;
+    }
+    unsigned int status = 0;
+    HCK(c, cudaMemcpyAsync(&status, &c->d_ctr->status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
+    if (dt_used)
+        HCK(c, cudaMemcpyAsync(dt_used, c->d_dt_log, sizeof(double) * nval, cudaMemcpyDeviceToHost,
+                               c->stream));
+    HCK(c, cudaStreamSynchronize(c->stream));
+    if (status) {
+        char buf[120];
+        snprintf(buf, sizeof buf, "non-positive or NaN %s detected", (status & STATUS_BAD_RHO) ? "density" : "energy");
+        return fail(c, HYDRO_ENEGATIVE, buf);
+    }
+    return HYDRO_OK;
+}
+
+hydro_status hydro_step(hydro_ctx* c, int nsteps, const double* dt_override) {
+    return hydro_step_dt(c, nsteps, dt_override, nullptr);
+}
+
+hydro_status hydro_step_profiled(hydro_ctx* c, int nsteps, double* kernel_ms) {
+    if (!c) return fail(nullptr, HYDRO_EINVAL, "ctx is NULL");
+    if (nsteps < 0 || !kernel_ms) return fail(c, HYDRO_EINVAL, "nsteps < 0 or kernel_ms is NULL");
+    std::vector<cudaEvent_t> ev(4 * (size_t)nsteps, nullptr);
+    hydro_status st = HYDRO_OK;
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { st = fail(c, HYDRO_ECUDA, "cudaEventCreate failed"); break; }
+    for (int s = 0; s < nsteps && st == HYDRO_OK; ++s) {
+        cudaError_t e = enqueue_step(c, (int)(c->step & 1), nullptr, nullptr, c->stream, &ev[4 * (size_t)s]);
+        if (e != cudaSuccess) st = fail_cuda(c, "profiled step", e);
+        else ++c->step;
+    }
+    if (st == HYDRO_OK) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = fail_cuda(c, "cudaStreamSynchronize", e);
+    }
+    for (int s = 0; s < nsteps && st == HYDRO_OK; ++s)
+        for (int k = 0; k < 3; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[4 * (size_t)s + k], ev[4 * (size_t)s + k + 1]);
+            kernel_ms[3 * (size_t)s + k] = ms;
+        }
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (st != HYDRO_OK) return st;
+    unsigned int status = 0;
+    HCK(c, cudaMemcpy(&status, &c->d_ctr->status, sizeof status, cudaMemcpyDeviceToHost));
+    if (status) return fail(c, HYDRO_ENEGATIVE, "non-positive or NaN density or energy detected");
+    return HYDRO_OK;
+}
+
+hydro_status hydro_cfl_dt(hydro_ctx* c, int grid, double* dt_out) {
+    hydro_status st = check_grid(c, grid);
+    if (st != HYDRO_OK) return st;
+    if (!dt_out) return fail(c, HYDRO_EINVAL, "dt_out is NULL");
+    DevCounters ctr;
+    GridRun run;
+    HCK(c, cudaMemcpyAsync(&ctr, c->d_ctr, sizeof ctr, cudaMemcpyDeviceToHost, c->stream));
+    HCK(c, cudaMemcpyAsync(&run, &c->d_run[grid], sizeof run, cudaMemcpyDeviceToHost, c->stream));
+    HCK(c, cudaStreamSynchronize(c->stream));
+    double w;
+    const unsigned long long bits = run.wmax[ctr.acc & 1u];
+    std::memcpy(&w, &bits, sizeof w);
+    *dt_out = c->cfl * c->gd[grid].h / w;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_get_time(hydro_ctx* c, int grid, double* t_out) {
+    hydro_status st = check_grid(c, grid);
+    if (st != HYDRO_OK) return st;
+    if (!t_out) return fail(c, HYDRO_EINVAL, "t_out is NULL");
+    HCK(c, cudaMemcpyAsync(t_out, &c->d_run[grid].t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HCK(c, cudaStreamSynchronize(c->stream));
+    return HYDRO_OK;
+}
+
+hydro_status hydro_get_step(hydro_ctx* c, long long* step_out) {
+    if (!c || !step_out) return fail(c, HYDRO_EINVAL, "ctx or step_out is NULL");
+    *step_out = c->step;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_set_step(hydro_ctx* c, long long step) {
+    if (!c) return fail(nullptr, HYDRO_EINVAL, "ctx is NULL");
+    if (step < 0) return fail(c, HYDRO_EINVAL, "step < 0");
+    c->step = step;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_set_time(hydro_ctx* c, int grid, double t) {
+    hydro_status st = check_grid(c, grid);
+    if (st != HYDRO_OK) return st;
+    if (!std::isfinite(t)) return fail(c, HYDRO_EINVAL, "t must be finite");
+    HCK(c, cudaMemcpyAsync(&c->d_run[grid].t, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    HCK(c, cudaStreamSynchronize(c->stream));
+    return HYDRO_OK;
+}
+
+hydro_status hydro_conservation(hydro_ctx* c, int grid, double sums[4]) {
+    hydro_status st = check_grid(c, grid);
+    if (st != HYDRO_OK) return st;
+    if (!sums) return fail(c, HYDRO_EINVAL, "sums is NULL");
+    const GridDesc& g = c->gd[grid];
+    if (c->prec == 64) HCK(c, launch_conservation<double>(state_ptr<double>(c), g, c->d_rows, c->d_out4, c->stream));
+    else HCK(c, launch_conservation<float>(state_ptr<float>(c), g, c->d_rows, c->d_out4, c->stream));
+    HCK(c, cudaMemcpyAsync(sums, c->d_out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HCK(c, cudaStreamSynchronize(c->stream));
+    return HYDRO_OK;
+}
+
+hydro_status hydro_get_stats(hydro_ctx* c, hydro_stats* out) {
+    if (!c || !out) return fail(c, HYDRO_EINVAL, "ctx or out is NULL");
+    DevCounters ctr;
+    HCK(c, cudaMemcpyAsync(&ctr, c->d_ctr, sizeof ctr, cudaMemcpyDeviceToHost, c->stream));
+    HCK(c, cudaStreamSynchronize(c->stream));
+    out->steps = (long long)ctr.steps;
+    out->riemann_fp64 = (long long)ctr.riemann_fp64;
+    out->status_flags = ctr.status;
+    return HYDRO_OK;
+}
+
+const char* hydro_last_error(const hydro_ctx* c) {
+    return c ? c->err.c_str() : g_init_error.c_str();
+}
+
+const char* hydro_version(void) { return "0.1.0"; }
+
+}  // extern "C"
