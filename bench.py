@@ -44,6 +44,8 @@ WORKLOADS = {
                        "2048x2048 Sedov blast, FP64, reflective, CFL 0.8, minmod, Newton Riemann (<=10 it)"),
     "sedov128_fp64": (lambda: [pr.sedov(128)], 64, "128x128 Sedov blast, FP64"),
     "sodx4096_fp64": (lambda: [pr.sod(4096, 16, 0)], 64, "4096x16 Sod tube along x, FP64"),
+    "modes4096_fp32": (lambda: [pr.random_modes(4096)], 32,
+                       "4096x4096 periodic random-mode field, FP32 (profiling size)"),
     "modes8192_fp32": (lambda: [pr.random_modes(8192)], 32,
                        "8192x8192 periodic random-mode field, FP32"),
     "modes8192_fp64": (lambda: [pr.random_modes(8192)], 64,

@@ -86,7 +86,8 @@ typedef struct {
 } hydro_params;
 
 /* Launch shape of the sweep kernels (all fields 0 = library default).
- *   tile_len      cells per tile along the sweep line (>= 4)
+ *   tile_len      cells per tile along the sweep line (>= 4); 0 chooses it per
+ *                 direction from a list-scheduling model of the tile queue
  *   ctas_per_sm   resident CTAs per SM of the persistent sweep launch
  *   graph_steps   steps captured per CUDA graph (even, 0 = no graph)
  * Results are bit-identical for every admissible setting. */

@@ -30,6 +30,7 @@ struct Consts {
     T G6;         // (g - 1) / (g + 1)
     T G7;         // (g - 1) / 2
     T inv_g;      // 1 / g
+    T hgp1;       // (g + 1) / 2
     T rho_floor;  // density floor
     T cf2g;       // c_floor^2 / g: p >= rho * cf2g
     T pmin;       // smallest pressure of the Riemann iteration, rho_floor * cf2g
@@ -48,6 +49,8 @@ __device__ __forceinline__ double tpow(double x, double e) { return pow(x, e); }
 __device__ __forceinline__ float tpow(float x, float e) { return __powf(x, e); }
 __device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double tabs(double x) { return fabs(x); }
 __device__ __forceinline__ float tabs(float x) { return fabsf(x); }
 
@@ -60,16 +63,22 @@ __device__ __forceinline__ T pow_or_one(T x, T e) {
 // ------------------------------------------------------------- EOS -----
 // Floors compare with '<' so a NaN passes through and is reported.
 template <class T>
-__device__ __forceinline__ Prim<T> cons_to_prim(const Consts<T>& K, const Cons<T>& U) {
+__device__ __forceinline__ Prim<T> cons_to_prim(const Consts<T>& K, const Cons<T>& U, T& ir) {
     Prim<T> W;
     W.r = (U.r < K.rho_floor) ? K.rho_floor : U.r;
-    const T ir = T(1) / W.r;
+    ir = T(1) / W.r;
     W.u = U.mn * ir;
     W.v = U.mt * ir;
     T p = K.gm1 * (U.E - T(0.5) * W.r * (W.u * W.u + W.v * W.v));
     const T pm = W.r * K.cf2g;
     W.p = (p < pm) ? pm : p;
     return W;
+}
+
+template <class T>
+__device__ __forceinline__ Prim<T> cons_to_prim(const Consts<T>& K, const Cons<T>& U) {
+    T ir;
+    return cons_to_prim(K, U, ir);
 }
 
 // ---------------------------------------------------- slopes and trace --
@@ -91,14 +100,14 @@ __device__ __forceinline__ T minmod(T a, T b) {
 // faces WL = W0 - D/2 + dW (left), WR = W0 + D/2 + dW (right), floored.
 template <class T>
 __device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) */,
-                                      const Prim<T>& Wm, const Prim<T>& W0,
+                                      const Prim<T>& Wm, const Prim<T>& W0, T ir0 /* 1/rho_0 */,
                                       const Prim<T>& Wp, Prim<T>& WL, Prim<T>& WR) {
     const T Dr = minmod(W0.r - Wm.r, Wp.r - W0.r);
     const T Du = minmod(W0.u - Wm.u, Wp.u - W0.u);
     const T Dv = minmod(W0.v - Wm.v, Wp.v - W0.v);
     const T Dp = minmod(W0.p - Wm.p, Wp.p - W0.p);
     const T dr = hdtdx * (W0.u * Dr + W0.r * Du);
-    const T du = hdtdx * (W0.u * Du + Dp / W0.r);
+    const T du = hdtdx * (W0.u * Du + Dp * ir0);
     const T dv = hdtdx * (W0.u * Dv);
     const T dp = hdtdx * (K.gamma * W0.p * Du + W0.u * Dp);
     WL.r = W0.r - T(0.5) * Dr + dr;
@@ -117,123 +126,174 @@ __device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) *
 }
 
 // ------------------------------------------------------ Riemann solver --
-// Pressure function of side K and its derivative (exact solver):
-//   shock (p > p_K):   f = (p - p_K) sqrt(A/(p+B)),  A = 2/((g+1) rho_K),
-//                      B = (g-1)/(g+1) p_K,  f' = sqrt(A/(p+B)) (1 - (p-p_K)/(2(p+B)))
-//   rarefaction:       f = 2 c_K/(g-1) ((p/p_K)^z - 1),
-//                      f' = (p/p_K)^(z-1) / (rho_K c_K)
+// Exact solver: Newton iteration on the pressure function
+//   F(p) = f_L(p) + f_R(p) + (u_R - u_L) = 0,
+//   shock (p > p_K):  f_K = (p - p_K) q,  q = sqrt(A_K/(p + B_K)),
+//                     A_K = 2/((g+1) rho_K), B_K = (g-1)/(g+1) p_K,
+//                     f_K' = q (1 - (p - p_K)/(2 (p + B_K)))
+//   rarefaction:      f_K = 2 c_K/(g-1) ((p/p_K)^z - 1),
+//                     f_K' = (p/p_K)^z / ((p/p_K) rho_K c_K).
+// The arithmetic is arranged for few divisions: each side carries 1/p_K and
+// 1/(rho_K c_K) = c_K/(g p_K); 1/(p + B) = q^2/A; and every derivative is
+// written f_K' = a_K/p + b_K so one division per step gives the Newton
+// update  dp = F p / (a_L + a_R + p (b_L + b_R)).
 template <class T>
-__device__ __forceinline__ void pressure_fn(const Consts<T>& K, T p, T rk, T pk, T ck,
-                                            T& f, T& df) {
-    if (p > pk) {
-        const T A = K.G5 / rk;
-        const T B = K.G6 * pk;
-        const T ipb = T(1) / (p + B);
-        const T q = tsqrt(A * ipb);
-        const T dpk = p - pk;
-        f = dpk * q;
-        df = q * (T(1) - T(0.5) * dpk * ipb);
+struct Side {
+    T r, u, v, p;  // traced state
+    T c;           // sound speed
+    T ip;          // 1 / p_K
+    T irc;         // 1 / (rho_K c_K)
+    T iA;          // 1 / A_K = (g+1)/2 rho_K
+    T B;           // B_K
+    T cG4;         // 2 c_K / (g-1)
+};
+
+template <class T>
+__device__ __forceinline__ Side<T> make_side(const Consts<T>& K, const Prim<T>& W) {
+    Side<T> s;
+    s.r = W.r; s.u = W.u; s.v = W.v; s.p = W.p;
+    T ir;
+    if (sizeof(T) == 8) {
+        const T irp = T(1) / (W.r * W.p);  // one division for 1/rho and 1/p
+        ir = W.p * irp;
+        s.ip = W.r * irp;
     } else {
-        const T r = p / pk;
-        const T pz = pow_or_one(r, K.z);
-        f = ck * K.G4 * (pz - T(1));
-        df = pz / (r * rk * ck);
+        ir = T(1) / W.r;
+        s.ip = T(1) / W.p;
+    }
+    s.c = tsqrt(K.gamma * W.p * ir);
+    s.irc = s.c * s.ip * K.inv_g;
+    s.iA = K.hgp1 * W.r;
+    s.B = K.G6 * W.p;
+    s.cG4 = s.c * K.G4;
+    return s;
+}
+
+// f_K(p) with f_K' = a/p + b; pz = (p/p_K)^z on the rarefaction branch, -1 on
+// the shock branch.  p == p_K gives f = 0 and pz = 1 exactly.
+template <class T>
+__device__ __forceinline__ void pressure_fn(const Consts<T>& K, const Side<T>& s, T p,
+                                            T& f, T& a, T& b, T& pz) {
+    if (p > s.p) {
+        const T q = trsqrt((p + s.B) * s.iA);
+        const T dpk = p - s.p;
+        f = dpk * q;
+        a = T(0);
+        b = q * (T(1) - T(0.5) * dpk * (q * q * s.iA));
+        pz = T(-1);
+    } else {
+        const bool one = (p == s.p);
+        const T r = one ? T(1) : p * s.ip;
+        pz = one ? T(1) : tpow(r, K.z);
+        f = s.cG4 * (pz - T(1));
+        a = pz * s.irc * s.p;
+        b = T(0);
     }
 }
 
 template <class T>
-struct Star { T p, u; bool floored; };
+struct Star {
+    T p, u;
+    T pzl, pzr;    // (p*/p_K)^z of each side, -1 where not evaluated
+    bool floored;  // the iterate reached the pressure floor
+};
 
-// (p*, u*) by Newton from p0 = (pL+pR)/2 - (uR-uL)(rhoL+rhoR)(cL+cR)/8, each
-// iterate clamped to pmin; at most niter steps, stopping once a step changes
-// p by no more than tol * p (the iterate is then converged to rounding, so
-// further steps would not move it); u* = (uL+uR)/2 + (f_R(p*) - f_L(p*))/2.
+// (p*, u*) by Newton from the PVRS estimate
+//   p0 = (pL+pR)/2 - (uR-uL)(rhoL+rhoR)(cL+cR)/8,
+// every iterate clamped to pmin, at most niter steps.  The iteration stops
+// once a step changes p by no more than tol * p: the iterate is then the
+// root to rounding, and f_K and (p/p_K)^z at the new iterate follow from
+// their values at the previous one by a first-order update (the neglected
+// term is O(tol^2)).  Without convergence f_K is evaluated again at the
+// last iterate.  u* = (uL+uR)/2 + (f_R(p*) - f_L(p*))/2.
 template <class T>
-__device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Prim<T>& L,
-                                                const Prim<T>& R, T cl, T cr) {
-    T p = T(0.5) * (L.p + R.p) - T(0.125) * (R.u - L.u) * (L.r + R.r) * (cl + cr);
+__device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T>& L,
+                                                const Side<T>& R) {
+    T p = T(0.5) * (L.p + R.p) - T(0.125) * (R.u - L.u) * (L.r + R.r) * (L.c + R.c);
     bool floored = false;
     if (p < K.pmin) { p = K.pmin; floored = true; }
     const T du = R.u - L.u;
-    T fl, dfl, fr, dfr;
+    T fl, al, bl, pzl, fr, ar, br, pzr;
+    bool conv = false;
     for (int it = 0; it < K.niter; ++it) {
-        pressure_fn(K, p, L.r, L.p, cl, fl, dfl);
-        pressure_fn(K, p, R.r, R.p, cr, fr, dfr);
-        T pn = p - (fl + fr + du) / (dfl + dfr);
-        if (pn < K.pmin) { pn = K.pmin; floored = true; }
-        const bool done = tabs(pn - p) <= K.tol * pn;
+        pressure_fn(K, L, p, fl, al, bl, pzl);
+        pressure_fn(K, R, p, fr, ar, br, pzr);
+        const T F = fl + fr + du;
+        const T g = F / ((al + ar) + p * (bl + br));   // Newton step / p
+        T d = g * p;                                    // the step p - p_new
+        T pn = p - d;
+        T rel = g;                                      // d / p
+        if (pn < K.pmin) { pn = K.pmin; floored = true; d = p - pn; rel = d / p; }
+        if (tabs(d) <= K.tol * pn) {
+            fl -= al * rel + bl * d;
+            fr -= ar * rel + br * d;
+            if (pzl > T(0)) pzl -= K.z * pzl * rel;
+            if (pzr > T(0)) pzr -= K.z * pzr * rel;
+            p = pn;
+            conv = true;
+            break;
+        }
         p = pn;
-        if (done) break;
     }
-    pressure_fn(K, p, L.r, L.p, cl, fl, dfl);
-    pressure_fn(K, p, R.r, R.p, cr, fr, dfr);
-    Star<T> s;
-    s.p = p;
-    s.u = T(0.5) * (L.u + R.u) + T(0.5) * (fr - fl);
-    s.floored = floored;
-    return s;
+    if (!conv) {
+        pressure_fn(K, L, p, fl, al, bl, pzl);
+        pressure_fn(K, R, p, fr, ar, br, pzr);
+    }
+    Star<T> st;
+    st.p = p;
+    st.u = T(0.5) * (L.u + R.u) + T(0.5) * (fr - fl);
+    st.pzl = pzl;
+    st.pzr = pzr;
+    st.floored = floored;
+    return st;
 }
 
 // State of the Riemann solution at x/t = 0.  0 <= u* takes the left side of
 // the contact (tangential velocity from the same side).  Left shock speed
 // S_L = u_L - c_L sqrt(zs p*/p_L + z); rarefaction head u_L - c_L, tail
 // u* - c*_L with c*_L = c_L (p*/p_L)^z.  Star densities: shock
-// rho_L (p*/p_L + G6)/(G6 p*/p_L + 1), rarefaction rho_L (p*/p_L)^(1/g).
-// Inside a fan at x/t = 0: c = G5 (c_L + G7 u_L), u = c (left);
-// c = G5 (c_R - G7 u_R), u = -c (right); rho = rho_K (c/c_K)^G4,
-// p = p_K (c/c_K)^G3.  Mirror formulas on the right.
+// rho_L (p*/p_L + G6)/(G6 p*/p_L + 1), rarefaction
+// rho_L (p*/p_L)^(1/g) = rho_L (p*/p_L) / ((p*/p_L)^z)^2.  Inside a fan at
+// x/t = 0: c = G5 (c_L + G7 u_L), u = c (left); c = G5 (c_R - G7 u_R), u = -c
+// (right); rho = rho_K (c/c_K)^G4, p = p_K (c/c_K)^G3.
 template <class T>
-__device__ __forceinline__ Prim<T> sample0(const Consts<T>& K, const Prim<T>& L,
-                                           const Prim<T>& R, T cl, T cr, const Star<T>& s) {
+__device__ __forceinline__ Prim<T> sample_side(const Consts<T>& K, const Side<T>& S, T pz,
+                                               const Star<T>& st, T sgn) {
+    // sgn = +1 for the left side, -1 for the right side (mirror formulas)
     Prim<T> W;
-    if (T(0) <= s.u) {
-        W.v = L.v;
-        const T pr = s.p / L.p;
-        if (s.p > L.p) {
-            const T sl = L.u - cl * tsqrt(K.zs * pr + K.z);
-            if (T(0) <= sl) { W.r = L.r; W.u = L.u; W.p = L.p; }
-            else { W.r = L.r * (pr + K.G6) / (K.G6 * pr + T(1)); W.u = s.u; W.p = s.p; }
-        } else {
-            const T shl = L.u - cl;
-            if (T(0) <= shl) { W.r = L.r; W.u = L.u; W.p = L.p; }
-            else {
-                const T cml = cl * pow_or_one(pr, K.z);
-                const T stl = s.u - cml;
-                if (T(0) > stl) { W.r = L.r * pow_or_one(pr, K.inv_g); W.u = s.u; W.p = s.p; }
-                else {
-                    const T c = K.G5 * (cl + K.G7 * L.u);
-                    const T cc = c / cl;
-                    W.u = c;
-                    W.r = L.r * tpow(cc, K.G4);
-                    W.p = L.p * tpow(cc, K.G3);
-                }
-            }
-        }
+    W.v = S.v;
+    const bool one = (st.p == S.p);
+    const T pr = one ? T(1) : st.p * S.ip;
+    if (st.p > S.p) {
+        const T sk = sgn * S.u - S.c * tsqrt(K.zs * pr + K.z);   // = sgn * S_K
+        if (T(0) <= sk) { W.r = S.r; W.u = S.u; W.p = S.p; }
+        else { W.r = S.r * (pr + K.G6) / (K.G6 * pr + T(1)); W.u = st.u; W.p = st.p; }
     } else {
-        W.v = R.v;
-        const T pr = s.p / R.p;
-        if (s.p > R.p) {
-            const T sr = R.u + cr * tsqrt(K.zs * pr + K.z);
-            if (T(0) >= sr) { W.r = R.r; W.u = R.u; W.p = R.p; }
-            else { W.r = R.r * (pr + K.G6) / (K.G6 * pr + T(1)); W.u = s.u; W.p = s.p; }
-        } else {
-            const T shr = R.u + cr;
-            if (T(0) >= shr) { W.r = R.r; W.u = R.u; W.p = R.p; }
-            else {
-                const T cmr = cr * pow_or_one(pr, K.z);
-                const T str = s.u + cmr;
-                if (T(0) <= str) { W.r = R.r * pow_or_one(pr, K.inv_g); W.u = s.u; W.p = s.p; }
-                else {
-                    const T c = K.G5 * (cr - K.G7 * R.u);
-                    const T cc = c / cr;
-                    W.u = -c;
-                    W.r = R.r * tpow(cc, K.G4);
-                    W.p = R.p * tpow(cc, K.G3);
-                }
+        const T hk = sgn * S.u - S.c;                              // head
+        if (T(0) <= hk) { W.r = S.r; W.u = S.u; W.p = S.p; }
+        else {
+            if (pz < T(0)) pz = one ? T(1) : tpow(pr, K.z);
+            const T tk = sgn * st.u - S.c * pz;                    // tail
+            if (T(0) > tk) {
+                W.r = one ? S.r : S.r * pr / (pz * pz);
+                W.u = st.u; W.p = st.p;
+            } else {
+                const T c = K.G5 * (S.c + sgn * K.G7 * S.u);
+                const T cc = c / S.c;
+                W.u = sgn * c;
+                W.r = S.r * tpow(cc, K.G4);
+                W.p = S.p * tpow(cc, K.G3);
             }
         }
     }
     return W;
+}
+
+template <class T>
+__device__ __forceinline__ Prim<T> sample0(const Consts<T>& K, const Side<T>& L,
+                                           const Side<T>& R, const Star<T>& st) {
+    if (T(0) <= st.u) return sample_side(K, L, st.pzl, st, T(1));
+    return sample_side(K, R, st.pzr, st, T(-1));
 }
 
 // Physical flux along the normal of a primitive state.
@@ -256,12 +316,12 @@ __device__ __forceinline__ T sound_speed(const Consts<T>& K, const Prim<T>& W) {
 
 // Godunov flux at one interface between the traced states L | R.
 template <class T>
-__device__ __forceinline__ Cons<T> godunov_flux_exact(const Consts<T>& K, const Prim<T>& L,
-                                                      const Prim<T>& R, bool* floored) {
-    const T cl = sound_speed(K, L), cr = sound_speed(K, R);
-    const Star<T> s = riemann_star(K, L, R, cl, cr);
+__device__ __forceinline__ Cons<T> godunov_flux_exact(const Consts<T>& K, const Prim<T>& WL,
+                                                      const Prim<T>& WR, bool* floored) {
+    const Side<T> L = make_side(K, WL), R = make_side(K, WR);
+    const Star<T> s = riemann_star(K, L, R);
     if (floored) *floored = s.floored;
-    return physical_flux(K, sample0(K, L, R, cl, cr, s));
+    return physical_flux(K, sample0(K, L, R, s));
 }
 
 }  // namespace hydro

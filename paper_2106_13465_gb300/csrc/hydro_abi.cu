@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -21,7 +22,7 @@ namespace {
 
 thread_local std::string g_init_error;
 
-constexpr int kDefaultTileLen = 64;
+constexpr int kDefaultTileLen = 0;  // 0: chosen per direction by auto_tile_len
 constexpr int kDefaultGraphSteps = 20;
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
@@ -41,6 +42,7 @@ Consts<T> make_consts(const hydro_params& p, double tol) {
     K.G6 = (T)((g - 1.0) / (g + 1.0));
     K.G7 = (T)((g - 1.0) / 2.0);
     K.inv_g = (T)(1.0 / g);
+    K.hgp1 = (T)((g + 1.0) / 2.0);
     K.rho_floor = (T)p.rho_floor;
     K.cf2g = (T)(p.c_floor * p.c_floor / g);
     K.pmin = (T)(p.rho_floor * (p.c_floor * p.c_floor / g));
@@ -80,6 +82,7 @@ struct hydro_ctx {
     size_t dt_log_cap = 0;
     hydro_tuning tuning{kDefaultTileLen, 0, kDefaultGraphSteps};
     int ctas[2] = {0, 0};       // CTAs per sweep launch (x, y)
+    int tile_len_used[2] = {0, 0};
     long long step = 0;         // steps since the last hydro_set_state
     cudaGraphExec_t gexec = nullptr;
     int gexec_steps = 0;
@@ -147,34 +150,65 @@ hydro_status validate_params(const hydro_params* p) {
 
 // Tile work-lists: for each grid, lines in groups of 32 (one per lane),
 // cells along the line in segments of tile_len.
-void build_tiles(const std::vector<GridDesc>& gd, int tile_len, std::vector<Tile> out[2]) {
-    for (int d = 0; d < 2; ++d) {
-        out[d].clear();
-        for (int g = 0; g < (int)gd.size(); ++g) {
-            const int nlines = d == DIR_X ? gd[g].ny : gd[g].nx;
-            const int n = d == DIR_X ? gd[g].nx : gd[g].ny;
-            for (int l0 = 0; l0 < nlines; l0 += kWarpLines)
-                for (int c0 = 0; c0 < n; c0 += tile_len)
-                    out[d].push_back(Tile{g, l0, c0, std::min(tile_len, n - c0)});
-        }
+void build_tiles(const std::vector<GridDesc>& gd, int dir, int tile_len, std::vector<Tile>& out) {
+    out.clear();
+    for (int g = 0; g < (int)gd.size(); ++g) {
+        const int nlines = dir == DIR_X ? gd[g].ny : gd[g].nx;
+        const int n = dir == DIR_X ? gd[g].nx : gd[g].ny;
+        for (int l0 = 0; l0 < nlines; l0 += kWarpLines)
+            for (int c0 = 0; c0 < n; c0 += tile_len)
+                out.push_back(Tile{g, l0, c0, std::min(tile_len, n - c0)});
     }
 }
 
+// Makespan of the dynamic tile queue on `warps` resident warps (list
+// scheduling in queue order), a tile of ncell cells costing ncell + 4 cell
+// units (its halo: two extra reads, one extra trace and interface solve).
+double list_schedule_makespan(const std::vector<Tile>& tiles, int warps) {
+    std::vector<double> heap(std::max(1, warps), 0.0);  // min-heap of warp finish times
+    std::make_heap(heap.begin(), heap.end(), std::greater<double>());
+    double span = 0.0;
+    for (const Tile& t : tiles) {
+        std::pop_heap(heap.begin(), heap.end(), std::greater<double>());
+        heap.back() += t.ncell + 4.0;
+        span = std::max(span, heap.back());
+        std::push_heap(heap.begin(), heap.end(), std::greater<double>());
+    }
+    return span;
+}
+
+int auto_tile_len(const std::vector<GridDesc>& gd, int dir, int warps) {
+    std::vector<int> cand;
+    for (int L = 16; L <= 128; L += 4) cand.push_back(L);
+    for (int L : {160, 192, 256, 384, 512}) cand.push_back(L);
+    int best = 64;
+    double best_span = 1e300;
+    std::vector<Tile> t;
+    for (int L : cand) {
+        build_tiles(gd, dir, L, t);
+        const double span = list_schedule_makespan(t, warps);
+        if (span < best_span * 0.999) { best_span = span; best = L; }
+    }
+    return best;
+}
+
 hydro_status upload_tiles(hydro_ctx* c) {
-    std::vector<Tile> t[2];
-    build_tiles(c->gd, c->tuning.tile_len, t);
     for (int d = 0; d < 2; ++d) {
-        if (c->d_tiles[d]) cudaFree(c->d_tiles[d]);
-        c->d_tiles[d] = nullptr;
-        HCK(c, cudaMalloc(&c->d_tiles[d], sizeof(Tile) * t[d].size()));
-        HCK(c, cudaMemcpy(c->d_tiles[d], t[d].data(), sizeof(Tile) * t[d].size(),
-                          cudaMemcpyHostToDevice));
-        c->ntiles[d] = (int)t[d].size();
         int per_sm = c->tuning.ctas_per_sm;
         if (per_sm <= 0)
             per_sm = c->prec == 64 ? sweep_ctas_per_sm<double>(d) : sweep_ctas_per_sm<float>(d);
         if (per_sm <= 0) per_sm = 1;
         const int warps_per_cta = kSweepThreads / 32;
+        const int resident_warps = c->nsm * per_sm * warps_per_cta;
+        const int L = c->tuning.tile_len > 0 ? c->tuning.tile_len : auto_tile_len(c->gd, d, resident_warps);
+        c->tile_len_used[d] = L;
+        std::vector<Tile> t;
+        build_tiles(c->gd, d, L, t);
+        if (c->d_tiles[d]) cudaFree(c->d_tiles[d]);
+        c->d_tiles[d] = nullptr;
+        HCK(c, cudaMalloc(&c->d_tiles[d], sizeof(Tile) * t.size()));
+        HCK(c, cudaMemcpy(c->d_tiles[d], t.data(), sizeof(Tile) * t.size(), cudaMemcpyHostToDevice));
+        c->ntiles[d] = (int)t.size();
         const int need = (c->ntiles[d] + warps_per_cta - 1) / warps_per_cta;
         c->ctas[d] = std::max(1, std::min(need, c->nsm * per_sm));
     }
@@ -383,8 +417,8 @@ void hydro_destroy(hydro_ctx* c) {
 hydro_status hydro_set_tuning(hydro_ctx* c, const hydro_tuning* t) {
     if (!c || !t) return fail(c, HYDRO_EINVAL, "ctx or tuning is NULL");
     hydro_tuning n = *t;
-    if (n.tile_len == 0) n.tile_len = kDefaultTileLen;
-    if (n.tile_len < 4 || n.tile_len > (1 << 24)) return fail(c, HYDRO_EINVAL, "tile_len must be in [4, 2^24]");
+    if (n.tile_len != 0 && (n.tile_len < 4 || n.tile_len > (1 << 24)))
+        return fail(c, HYDRO_EINVAL, "tile_len must be 0 (automatic) or in [4, 2^24]");
     if (n.ctas_per_sm < 0 || n.ctas_per_sm > 64) return fail(c, HYDRO_EINVAL, "ctas_per_sm must be in [0, 64]");
     if (n.graph_steps < 0 || (n.graph_steps & 1) || n.graph_steps > 1000)
         return fail(c, HYDRO_EINVAL, "graph_steps must be even and in [0, 1000]");

@@ -14,17 +14,23 @@ __device__ __forceinline__ Cons<float> FluxOp<float>::eval(const SweepArgs<float
                                                            const Prim<float>& L,
                                                            const Prim<float>& R, unsigned& nfb) {
     const Consts<float>& K = a.K;
-    const float cl = sound_speed(K, L), cr = sound_speed(K, R);
-    const Star<float> s = riemann_star(K, L, R, cl, cr);
     const float pmn = (L.p < R.p) ? L.p : R.p;
     const float pmx = (L.p < R.p) ? R.p : L.p;
-    if (s.floored || pmn < 1e-6f * pmx || s.p < 1e-3f * pmn) {
+    Star<float> s;
+    Side<float> SL, SR;
+    const bool near_vacuum_states = pmn < 1e-6f * pmx;
+    if (!near_vacuum_states) {
+        SL = make_side(K, L);
+        SR = make_side(K, R);
+        s = riemann_star(K, SL, SR);
+    }
+    if (near_vacuum_states || s.floored || s.p < 1e-3f * pmn) {
         ++nfb;
         const Prim<double> Ld = {L.r, L.u, L.v, L.p}, Rd = {R.r, R.u, R.v, R.p};
         const Cons<double> F = flux_fp64_near_vacuum(&a.Kd, Ld, Rd);
         return Cons<float>{(float)F.r, (float)F.mn, (float)F.mt, (float)F.E};
     }
-    return physical_flux(K, sample0(K, L, R, cl, cr, s));
+    return physical_flux(K, sample0(K, SL, SR, s));
 }
 
 template <class T>

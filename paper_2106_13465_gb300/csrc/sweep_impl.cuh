@@ -108,16 +108,18 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs<T>
         // window at i = s0 - 2: u0 = U_i, u1 = U_{i+1}
         Cons<T> u0 = load_cell<T, DIR>(src, stride, g.plane, s0 - 2, n, bclo, bchi);
         Cons<T> u1 = load_cell<T, DIR>(src, stride, g.plane, s0 - 1, n, bclo, bchi);
-        Prim<T> w0 = cons_to_prim(K, u0), w1 = cons_to_prim(K, u1);
+        T ir1;
+        Prim<T> w0 = cons_to_prim(K, u0), w1 = cons_to_prim(K, u1, ir1);
         Prim<T> wr0 = w0;          // right face of cell i (set from i = s0 - 1 on)
         Cons<T> flo = {T(0), T(0), T(0), T(0)};  // flux at i - 1/2
         T smax = T(0);
 
         for (int i = s0 - 2; i < s1; ++i) {
             const Cons<T> u2 = load_cell<T, DIR>(src, stride, g.plane, i + 2, n, bclo, bchi);
-            const Prim<T> w2 = cons_to_prim(K, u2);
+            T ir2;
+            const Prim<T> w2 = cons_to_prim(K, u2, ir2);
             Prim<T> wl1, wr1;
-            trace(K, hdtdx, w0, w1, w2, wl1, wr1);          // cell i + 1
+            trace(K, hdtdx, w0, w1, ir1, w2, wl1, wr1);     // cell i + 1
             Cons<T> fhi = flo;
             if (i >= s0 - 1) fhi = FluxOp<T>::eval(a, wr0, wl1, nfb);  // interface i + 1/2
             if (i >= s0) {
@@ -136,16 +138,17 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs<T>
                     bad |= (out.E > T(0)) ? 0u : STATUS_BAD_E;
                     if (a.which == 1) {
                         // CFL wave speed of the new state (next step's dt)
-                        const Prim<T> w = cons_to_prim(K, out);
+                        T ir;
+                        const Prim<T> w = cons_to_prim(K, out, ir);
                         const T au = tabs(w.u), av = tabs(w.v);
-                        const T s = ((au > av) ? au : av) + sound_speed(K, w);
+                        const T s = ((au > av) ? au : av) + tsqrt(K.gamma * w.p * ir);
                         smax = (s <= smax) ? smax : s;
                     }
                 }
             }
             flo = fhi;
             u0 = u1; u1 = u2;
-            w0 = w1; w1 = w2;
+            w0 = w1; w1 = w2; ir1 = ir2;
             wr0 = wr1;
         }
 
