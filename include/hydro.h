@@ -41,7 +41,7 @@ typedef enum {
     HYDRO_ENOMEM = 2,    /* device or host allocation failed */
     HYDRO_ECUDA = 3,     /* a CUDA runtime call failed (no device, launch error) */
     HYDRO_ENEGATIVE = 4, /* a non-positive or NaN density or energy appeared */
-    HYDRO_ETIMEOUT = 5   /* a bounded device-side wait gave up (reserved) */
+    HYDRO_ETIMEOUT = 5   /* a bounded device-side wait (TMA copy) gave up */
 } hydro_status;
 
 /* Boundary conditions of one side (§1/Fig. 5 "apply boundary conditions";
@@ -86,8 +86,9 @@ typedef struct {
 } hydro_params;
 
 /* Launch shape of the sweep kernels (all fields 0 = library default).
- *   tile_len      cells per tile along the sweep line (>= 4); 0 chooses it per
- *                 direction from a list-scheduling model of the tile queue
+ *   tile_len      cells per tile along the sweep line (a multiple of 4); 0
+ *                 chooses it per direction from a list-scheduling model of
+ *                 the tile queue
  *   ctas_per_sm   resident CTAs per SM of the persistent sweep launch
  *   graph_steps   steps captured per CUDA graph (even, 0 = no graph)
  * Results are bit-identical for every admissible setting. */
@@ -101,7 +102,8 @@ typedef struct {
  *   steps          completed steps
  *   riemann_fp64   FP32 contexts: interface solves redone in FP64 near vacuum
  *   status_flags   bit 0: non-positive/NaN density, bit 1: non-positive/NaN
- *                  energy (sticky until hydro_set_state) */
+ *                  energy, bit 2: a bounded wait timed out (sticky until
+ *                  hydro_set_state) */
 typedef struct {
     long long steps;
     long long riemann_fp64;

@@ -21,7 +21,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # square root and power (FP64 operations stay IEEE)
 EXTRA = {"sweep_f32.cu": ["--use_fast_math"]}
 SOURCES = ["hydro_abi.cu", "aux.cu", "sweep_f64.cu", "sweep_f32.cu"]
-HEADERS = ["godunov.cuh", "kernels.h", "sweep_impl.cuh"]
+HEADERS = ["godunov.cuh", "kernels.h", "sweep_tma.cuh"]
 
 
 def nvcc() -> str:

@@ -26,6 +26,10 @@ __global__ void step_prologue_kernel(GridRun* run, const GridDesc* grids, int ng
         ctr->acc = dst;
         ctr->tile_ctr[0] = 0u;
         ctr->tile_ctr[1] = 0u;
+        ctr->redo_count[0] = 0u;
+        ctr->redo_count[1] = 0u;
+        ctr->redo_claim[0] = 0u;
+        ctr->redo_claim[1] = 0u;
         ctr->steps += 1ull;
     }
 }

@@ -2,6 +2,8 @@
 // work-lists, the step driver (§1, Fig. 5: per step a dt, then a sweep along
 // each direction, the order alternating), CUDA-graph capture of the step
 // loop, state transfer and diagnostics.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -80,6 +82,10 @@ struct hydro_ctx {
     size_t dt_ovr_cap = 0;
     double* d_dt_log = nullptr;
     size_t dt_log_cap = 0;
+    CUtensorMap* d_maps = nullptr;  // [grid][buffer][dir]
+    int* d_redo = nullptr;          // [2][redo_cap] FP32 second-pass tile lists
+    int redo_cap = 0;
+    int ctas_redo[2] = {0, 0};
     hydro_tuning tuning{kDefaultTileLen, 0, kDefaultGraphSteps};
     int ctas[2] = {0, 0};       // CTAs per sweep launch (x, y)
     int tile_len_used[2] = {0, 0};
@@ -192,12 +198,50 @@ int auto_tile_len(const std::vector<GridDesc>& gd, int dir, int warps) {
     return best;
 }
 
+// TMA tensor maps of every grid over both state buffers (see kernels.h).
+hydro_status build_tensor_maps(hydro_ctx* c) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(c, HYDRO_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const size_t nmaps = c->gd.size() * 4;
+    std::vector<CUtensorMap> maps(nmaps);
+    const CUtensorMapDataType dtype = c->prec == 64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint32_t cx = (cuuint32_t)(16 / c->esz);
+    for (size_t g = 0; g < c->gd.size(); ++g) {
+        const GridDesc& d = c->gd[g];
+        const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, 4};
+        const cuuint64_t strides[2] = {(cuuint64_t)d.pitch * c->esz, (cuuint64_t)d.plane * c->esz};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        for (int b = 0; b < 2; ++b) {
+            void* base = (char*)c->buf[b] + (size_t)d.off * c->esz;
+            for (int dir = 0; dir < 2; ++dir) {
+                const cuuint32_t box[3] = {dir == DIR_X ? cx : 32u, dir == DIR_X ? 32u : 4u, 4u};
+                CUresult r = encode(&maps[(g * 2 + b) * 2 + dir], dtype, 3, base, dims, strides, box, estr,
+                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) {
+                    char buf[160];
+                    snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for grid %zu", (int)r, g);
+                    return fail(c, HYDRO_ECUDA, buf);
+                }
+            }
+        }
+    }
+    HCK(c, cudaMalloc(&c->d_maps, sizeof(CUtensorMap) * nmaps));
+    HCK(c, cudaMemcpy(c->d_maps, maps.data(), sizeof(CUtensorMap) * nmaps, cudaMemcpyHostToDevice));
+    return HYDRO_OK;
+}
+
 hydro_status upload_tiles(hydro_ctx* c) {
     for (int d = 0; d < 2; ++d) {
+        const int var = c->prec == 64 ? VAR_F64 : VAR_F32_MAIN;
         int per_sm = c->tuning.ctas_per_sm;
-        if (per_sm <= 0)
-            per_sm = c->prec == 64 ? sweep_ctas_per_sm<double>(d) : sweep_ctas_per_sm<float>(d);
-        if (per_sm <= 0) per_sm = 1;
+        const int occ = c->prec == 64 ? sweep_ctas_per_sm<double>(d, var) : sweep_ctas_per_sm<float>(d, var);
+        if (occ <= 0) return fail(c, HYDRO_ECUDA, "sweep kernel cannot be resident on an SM");
+        if (per_sm <= 0 || per_sm > occ) per_sm = occ;
         const int warps_per_cta = kSweepThreads / 32;
         const int resident_warps = c->nsm * per_sm * warps_per_cta;
         const int L = c->tuning.tile_len > 0 ? c->tuning.tile_len : auto_tile_len(c->gd, d, resident_warps);
@@ -211,6 +255,21 @@ hydro_status upload_tiles(hydro_ctx* c) {
         c->ntiles[d] = (int)t.size();
         const int need = (c->ntiles[d] + warps_per_cta - 1) / warps_per_cta;
         c->ctas[d] = std::max(1, std::min(need, c->nsm * per_sm));
+        if (c->prec == 32) {
+            const int occ2 = sweep_ctas_per_sm<float>(d, VAR_F32_REDO);
+            if (occ2 <= 0) return fail(c, HYDRO_ECUDA, "second-pass kernel cannot be resident on an SM");
+            c->ctas_redo[d] = std::max(1, std::min(need, c->nsm * occ2));
+        }
+    }
+    if (c->prec == 32) {
+        const int cap = std::max(c->ntiles[0], c->ntiles[1]);
+        if (cap > c->redo_cap) {
+            cudaFree(c->d_redo);
+            c->d_redo = nullptr;
+            c->redo_cap = 0;
+            HCK(c, cudaMalloc(&c->d_redo, sizeof(int) * 2 * (size_t)cap));
+            c->redo_cap = cap;
+        }
     }
     return HYDRO_OK;
 }
@@ -228,8 +287,12 @@ SweepArgs<T> sweep_args(hydro_ctx* c, int which, const Consts<T>& K) {
     a.dst = (T*)c->buf[which ^ 1];
     a.grids = c->d_grids;
     a.tiles = nullptr;
+    a.maps = c->d_maps;
     a.ntiles = 0;
     a.which = which;
+    a.src_buf = which;
+    a.redo_list = c->d_redo;
+    a.redo_cap = c->redo_cap;
     a.run = c->d_run;
     a.ctr = c->d_ctr;
     a.K = K;
@@ -253,7 +316,13 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
         SweepArgs<T> a = sweep_args<T>(c, which, K);
         a.tiles = c->d_tiles[dir];
         a.ntiles = c->ntiles[dir];
-        e = launch_sweep<T>(dir, a, c->ctas[dir], s);
+        if (sizeof(T) == 8) {
+            e = launch_sweep<T>(dir, VAR_F64, a, c->ctas[dir], s);
+        } else {
+            // main FP32 pass, then the second pass over tiles it queued
+            e = launch_sweep<T>(dir, VAR_F32_MAIN, a, c->ctas[dir], s);
+            if (e == cudaSuccess) e = launch_sweep<T>(dir, VAR_F32_REDO, a, c->ctas_redo[dir], s);
+        }
         if (e != cudaSuccess) return e;
         if (ev && (e = cudaEventRecord(ev[2 + which], s)) != cudaSuccess) return e;
     }
@@ -298,6 +367,17 @@ hydro_status check_grid(hydro_ctx* c, int grid) {
 
 template <class T>
 T* state_ptr(hydro_ctx* c) { return (T*)c->buf[0]; }
+
+hydro_status status_result(hydro_ctx* c, unsigned int status) {
+    if (status & STATUS_TIMEOUT)
+        return fail(c, HYDRO_ETIMEOUT, "a bounded wait for a TMA copy gave up (sweep kernel)");
+    if (status) {
+        char buf[120];
+        snprintf(buf, sizeof buf, "non-positive or NaN %s detected", (status & STATUS_BAD_RHO) ? "density" : "energy");
+        return fail(c, HYDRO_ENEGATIVE, buf);
+    }
+    return HYDRO_OK;
+}
 
 }  // namespace
 
@@ -389,6 +469,7 @@ hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
     if (e == cudaSuccess) e = cudaMemset(c->buf[0], 0, c->buf_elems * c->esz);
     if (e == cudaSuccess) e = cudaMemset(c->buf[1], 0, c->buf_elems * c->esz);
     if (e != cudaSuccess) { fail_cuda(c, "context set-up", e); return bail(HYDRO_ECUDA); }
+    if ((st = build_tensor_maps(c)) != HYDRO_OK) return bail(st);
     if ((st = upload_tiles(c)) != HYDRO_OK) return bail(st);
 
     *out = c;
@@ -409,6 +490,8 @@ void hydro_destroy(hydro_ctx* c) {
     cudaFree(c->d_out4);
     cudaFree(c->d_dt_ovr);
     cudaFree(c->d_dt_log);
+    cudaFree(c->d_maps);
+    cudaFree(c->d_redo);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -417,8 +500,8 @@ void hydro_destroy(hydro_ctx* c) {
 hydro_status hydro_set_tuning(hydro_ctx* c, const hydro_tuning* t) {
     if (!c || !t) return fail(c, HYDRO_EINVAL, "ctx or tuning is NULL");
     hydro_tuning n = *t;
-    if (n.tile_len != 0 && (n.tile_len < 4 || n.tile_len > (1 << 24)))
-        return fail(c, HYDRO_EINVAL, "tile_len must be 0 (automatic) or in [4, 2^24]");
+    if (n.tile_len != 0 && (n.tile_len < 4 || n.tile_len > (1 << 24) || (n.tile_len & 3)))
+        return fail(c, HYDRO_EINVAL, "tile_len must be 0 (automatic) or a multiple of 4 in [4, 2^24]");
     if (n.ctas_per_sm < 0 || n.ctas_per_sm > 64) return fail(c, HYDRO_EINVAL, "ctas_per_sm must be in [0, 64]");
     if (n.graph_steps < 0 || (n.graph_steps & 1) || n.graph_steps > 1000)
         return fail(c, HYDRO_EINVAL, "graph_steps must be even and in [0, 1000]");
@@ -530,12 +613,7 @@ hydro_status hydro_step_dt(hydro_ctx* c, int nsteps, const double* dt_override, 
         HCK(c, cudaMemcpyAsync(dt_used, c->d_dt_log, sizeof(double) * nval, cudaMemcpyDeviceToHost,
                                c->stream));
     HCK(c, cudaStreamSynchronize(c->stream));
-    if (status) {
-        char buf[120];
-        snprintf(buf, sizeof buf, "non-positive or NaN %s detected", (status & STATUS_BAD_RHO) ? "density" : "energy");
-        return fail(c, HYDRO_ENEGATIVE, buf);
-    }
-    return HYDRO_OK;
+    return status_result(c, status);
 }
 
 hydro_status hydro_step(hydro_ctx* c, int nsteps, const double* dt_override) {
@@ -569,8 +647,7 @@ hydro_status hydro_step_profiled(hydro_ctx* c, int nsteps, double* kernel_ms) {
     if (st != HYDRO_OK) return st;
     unsigned int status = 0;
     HCK(c, cudaMemcpy(&status, &c->d_ctr->status, sizeof status, cudaMemcpyDeviceToHost));
-    if (status) return fail(c, HYDRO_ENEGATIVE, "non-positive or NaN density or energy detected");
-    return HYDRO_OK;
+    return status_result(c, status);
 }
 
 hydro_status hydro_cfl_dt(hydro_ctx* c, int grid, double* dt_out) {

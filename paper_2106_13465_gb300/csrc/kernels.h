@@ -10,7 +10,15 @@
 //   a multiple of 32 elements, plane_g = ny * pitch_g, off_g 256-B aligned.
 // Interior cells only: the 2 ghost cells per side along the sweep axis are
 // formed while a line is read (boundary conditions folded into the load).
+//
+// Each grid and buffer also has two TMA tensor maps over this layout, a 3D
+// tensor (x, y, q) of extents (nx, ny, 4) with byte strides
+// (pitch * esz, plane * esz):
+//   x-sweep map: box (16 bytes of x, 32 rows, 4 planes)  -- 32 lines x C cells
+//   y-sweep map: box (32 columns, 4 rows, 4 planes)      -- 32 lines x 4 cells
+// stored at maps[(grid * 2 + buffer) * 2 + dir].
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,10 +28,25 @@ namespace hydro {
 
 enum { BC_REFLECT = 0, BC_TRANSMISSIVE = 1, BC_PERIODIC = 2 };
 enum { DIR_X = 0, DIR_Y = 1 };
-enum { STATUS_BAD_RHO = 1u, STATUS_BAD_E = 2u };
+enum { STATUS_BAD_RHO = 1u, STATUS_BAD_E = 2u, STATUS_TIMEOUT = 4u };
+
+// kernel variants: FP64; FP32 main pass (tiles with a near-vacuum interface
+// are queued for a second pass); FP32 second pass (FP64 near vacuum)
+enum { VAR_F64 = 0, VAR_F32_MAIN = 1, VAR_F32_REDO = 2 };
 
 constexpr int kWarpLines = 32;      // lines per warp tile (one per lane)
 constexpr int kSweepThreads = 128;  // threads per CTA of the sweep kernels
+
+// cells per TMA chunk along the sweep line and ring depth per warp
+template <class T>
+__host__ __device__ constexpr int chunk_cells(int dir) { return dir == DIR_X ? 16 / (int)sizeof(T) : 4; }
+__host__ __device__ constexpr int ring_slots(int dir) { return dir == DIR_X ? 6 : 4; }
+template <class T>
+__host__ __device__ constexpr int slot_bytes(int dir) { return 4 * 32 * chunk_cells<T>(dir) * (int)sizeof(T); }
+template <class T>
+__host__ __device__ constexpr int sweep_smem_bytes(int dir) {
+    return (kSweepThreads / 32) * ring_slots(dir) * (slot_bytes<T>(dir) + 8);
+}
 
 struct GridDesc {
     long long off;    // element offset of plane 0 in a state buffer
@@ -49,9 +72,11 @@ struct GridRun {
 
 // Context-wide device counters.
 struct DevCounters {
-    unsigned int acc;          // wmax slot holding the current state's speed
-    unsigned int status;       // sticky STATUS_* flags
-    unsigned int tile_ctr[2];  // work counters of the two sweeps of a step
+    unsigned int acc;            // wmax slot holding the current state's speed
+    unsigned int status;         // sticky STATUS_* flags
+    unsigned int tile_ctr[2];    // work counters of the two sweeps of a step
+    unsigned int redo_count[2];  // tiles queued for the FP32 second pass
+    unsigned int redo_claim[2];  // work counters of the second pass
     unsigned long long steps;
     unsigned long long riemann_fp64;
 };
@@ -62,21 +87,26 @@ struct SweepArgs {
     T* dst;
     const GridDesc* grids;
     const Tile* tiles;
+    const CUtensorMap* maps;
     int ntiles;
     int which;       // 0: first sweep of the step, 1: second (folds in CFL max)
+    int src_buf;     // buffer index of src (its tensor maps)
+    int* redo_list;  // [2][redo_cap] tile indices for the FP32 second pass
+    int redo_cap;
     GridRun* run;
     DevCounters* ctr;
     Consts<T> K;
     Consts<double> Kd;  // FP64 constants (the FP32 path's near-vacuum solves)
 };
 
-// Resident CTAs per SM of the sweep kernel (occupancy calculator).
+// Resident CTAs per SM of a sweep kernel variant (occupancy calculator,
+// including its dynamic shared memory).
 template <class T>
-int sweep_ctas_per_sm(int dir);
+int sweep_ctas_per_sm(int dir, int var);
 
 // ---- launchers (defined in the kernel translation units) ------------------
 template <class T>
-cudaError_t launch_sweep(int dir, const SweepArgs<T>& a, int nctas, cudaStream_t s);
+cudaError_t launch_sweep(int dir, int var, const SweepArgs<T>& a, int nctas, cudaStream_t s);
 
 cudaError_t launch_step_prologue(GridRun* run, const GridDesc* grids, int ngrids,
                                  DevCounters* ctr, const double* dt_override, double cfl,

@@ -1,20 +1,21 @@
 // sweep_f64.cu -- FP64 instantiation of the fused sweep kernel (IEEE double
 // division, square root and power throughout).
-#include "sweep_impl.cuh"
+#include "sweep_tma.cuh"
 
 namespace hydro {
 
-template <class T>
-int sweep_ctas_per_sm(int dir) {
-    int n = 0;
-    if (dir == DIR_X)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, DIR_X>, kSweepThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, DIR_Y>, kSweepThreads, 0);
-    return n;
+template <>
+cudaError_t launch_sweep<double>(int dir, int var, const SweepArgs<double>& a, int nctas, cudaStream_t s) {
+    (void)var;
+    if (nctas <= 0) return cudaSuccess;
+    if (dir == DIR_X) return launch_one<double, DIR_X, VAR_F64>(a, nctas, s);
+    return launch_one<double, DIR_Y, VAR_F64>(a, nctas, s);
 }
 
-template cudaError_t launch_sweep<double>(int, const SweepArgs<double>&, int, cudaStream_t);
-template int sweep_ctas_per_sm<double>(int);
+template <>
+int sweep_ctas_per_sm<double>(int dir, int var) {
+    (void)var;
+    return dir == DIR_X ? occupancy_one<double, DIR_X, VAR_F64>() : occupancy_one<double, DIR_Y, VAR_F64>();
+}
 
 }  // namespace hydro

@@ -90,9 +90,10 @@ def test_random_modes_256_periodic_fp64():
 
 @pytest.mark.parametrize("nx,ny,bc,tile", [
     (37, 53, (P_, P_, R_, R_), 16),
-    (53, 37, (T_, T_, P_, P_), 7),
+    (53, 37, (T_, T_, P_, P_), 8),
     (100, 33, (R_, T_, T_, R_), 64),
-    (65, 65, (R_, R_, R_, R_), 5),
+    (65, 65, (R_, R_, R_, R_), 4),
+    (67, 70, (P_, P_, T_, T_), 12),
 ])
 def test_ragged_sizes_and_mixed_boundaries(nx, ny, bc, tile):
     pb = pr.random_modes(nx, ny, seed=nx * 1000 + ny)
@@ -121,14 +122,48 @@ def test_uniform_state_bit_exact_on_gpu():
         assert dts[0] == pytest.approx(0.8 * pb.h / (max(abs(u), abs(v)) + c), rel=1e-15)
 
 
-def test_results_identical_for_every_tile_shape_schedule_and_graph():
+@pytest.mark.parametrize("precision", [64, 32])
+def test_results_identical_for_every_tile_shape_schedule_and_graph(precision):
     pb = pr.random_modes(150, 97, seed=21)
     pb.bc = (P_, P_, R_, R_)
-    ref, _, _ = gpu_run(pb, 22, tuning=dict(tile_len=64, ctas_per_sm=0, graph_steps=20), record=False)
-    for tl, cps, gs in [(4, 0, 0), (5, 1, 2), (16, 3, 20), (97, 0, 10), (4096, 2, 0)]:
-        got, _, _ = gpu_run(pb, 22, tuning=dict(tile_len=tl, ctas_per_sm=cps, graph_steps=gs),
-                            record=False)
+    ref, _, _ = gpu_run(pb, 22, precision=precision,
+                        tuning=dict(tile_len=64, ctas_per_sm=0, graph_steps=20), record=False)
+    for tl, cps, gs in [(4, 0, 0), (8, 1, 2), (16, 3, 20), (100, 0, 10), (4096, 2, 0), (0, 0, 20)]:
+        got, _, _ = gpu_run(pb, 22, precision=precision,
+                            tuning=dict(tile_len=tl, ctas_per_sm=cps, graph_steps=gs), record=False)
         assert np.array_equal(got, ref), (tl, cps, gs)
+
+
+def _vacuum_pair(n=64, ny=6):
+    """Two streams leaving each other: a strong double rarefaction whose
+    interfaces need the FP64 solve in the FP32 path."""
+    x = (np.arange(n) + 0.5) / n
+    u = np.where(x < 0.5, -2.0, 2.0)
+    U = pr.conserved(np.ones((ny, n)), np.tile(u, (ny, 1)), 0.0, 0.4)
+    return pr.Problem("123", U, 1.0 / n, (T_,) * 4)
+
+
+def test_fp32_second_pass_results_independent_of_tiling_and_batching():
+    """Tiles holding a near-vacuum interface are recomputed by the second
+    pass; results do not depend on which tiles that is."""
+    pbs = [_vacuum_pair(), pr.random_modes(70, 40, seed=3), pr.transpose(_vacuum_pair(48, 9))]
+    grids = [(p.nx, p.ny, p.h, p.bc) for p in pbs]
+    dts = np.full((5, len(pbs)), 0.2 / 64)
+    outs = {}
+    for tl in (4, 16, 0):
+        with H.Context(grids, precision=32) as c:
+            c.set_tuning(tile_len=tl)
+            for g, p in enumerate(pbs):
+                c.set_state(g, p.U)
+            c.step(5, dt_override=dts)
+            outs[tl] = [c.get_state(g) for g in range(len(pbs))]
+            assert c.stats()["riemann_fp64"] > 0
+    for tl in (16, 0):
+        for g in range(len(pbs)):
+            assert np.array_equal(outs[tl][g], outs[4][g]), (tl, g)
+    for g, p in enumerate(pbs):
+        single, _, _ = gpu_run(p, 5, precision=32, dt_override=dts[:, g], record=False)
+        assert np.array_equal(single, outs[0][g]), g
 
 
 def test_batched_grids_match_oracle_and_single_grid_runs():
@@ -222,11 +257,7 @@ def test_fp32_density_error_against_fp64_with_replayed_dt():
 def test_fp32_near_vacuum_interfaces_use_fp64():
     """Two streams leaving each other (strong double rarefaction) push p*
     toward zero; those interfaces are solved again in FP64."""
-    n = 64
-    x = (np.arange(n) + 0.5) / n
-    u = np.where(x < 0.5, -2.0, 2.0)
-    U = pr.conserved(np.ones((4, n)), np.tile(u, (4, 1)), 0.0, 0.4)
-    pb = pr.Problem("123", U, 1.0 / n, (T_,) * 4)
+    pb = _vacuum_pair(64, 4)
     ref, dts, _ = O.run(pb.U, pb.h, pb.bc, 5)
     got, _, stats = gpu_run(pb, 5, precision=32, dt_override=dts)
     assert stats["riemann_fp64"] > 0
