@@ -66,27 +66,33 @@ def load_peaks() -> dict:
         return {}
 
 
+SWEEP_SOURCES = ("godunov.cuh", "kernels.h", "sweep_tma.cuh", "sweep_f64.cu", "sweep_f32.cu")
+
+# FP64 pipe of a GB300: 152 SMs x 2 DFMA per clock x 2 flops x 2070 MHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2106_13465_gb300", "csrc"))):
+    for f in SWEEP_SOURCES:
         with open(os.path.join(ROOT, "paper_2106_13465_gb300", "csrc", f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current kernel sources; else None."""
+def recorded_profile(workload: str) -> dict:
+    """Figures of the committed ncu summary for this workload's sweep kernel,
+    if they were taken on the current kernel sources; else {}."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
-        return None
+        return {}
     ent = rec.get(workload)
     if not ent or ent.get("source_hash") != kernel_source_hash():
-        return None
-    return ent.get("dram_bytes_per_sweep")
+        return {}
+    return ent
 
 
 # ---------------------------------------------------------------- clocks --
@@ -298,14 +304,26 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # ---- roofline of the dominant kernel (the sweep) ----------------------
     peaks = load_peaks()
+    prof = recorded_profile(wl)
+    alg_bytes = float(state_bytes)  # one read + one write of 4 planes per sweep = 2 x (state / 2)
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
-    alg_bytes = 2 * state_bytes / 2  # one read + one write of the 4 planes per sweep
-    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": recorded_traffic(wl),
-                "kernel": "sweep_kernel", "launch_ms": sweep_ms,
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"}
+    hbm_achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+    hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+           "frac": hbm_achieved / hbm_peak,
+           "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"}
+    flops_cell = prof.get("fp64_flops_per_cell_sweep")
+    if prec == 64 and flops_cell:
+        # FP64-pipe bound: flops per cell-sweep counted by ncu on this kernel
+        achieved = flops_cell * cells / (sweep_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": prof.get("dram_bytes_per_sweep"),
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)",
+                    "flops_per_cell_sweep": flops_cell, "hbm_view": hbm}
+    else:
+        roofline = dict(hbm)
+        roofline["traffic"] = prof.get("dram_bytes_per_sweep")
+    roofline.update({"kernel": "sweep_kernel", "launch_ms": sweep_ms,
+                     "algorithmic_bytes_per_launch": alg_bytes})
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
