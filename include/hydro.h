@@ -176,6 +176,33 @@ hydro_status hydro_set_time(hydro_ctx *ctx, int grid, double t);
  * `grid`, in FP64 and in a fixed summation order (bit-reproducible). */
 hydro_status hydro_conservation(hydro_ctx *ctx, int grid, double sums[4]);
 
+/* Domain totals h^2 * sum over cells of each conserved variable of a state
+ * the caller holds on the device, computed without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they run (work recorded into a stream
+ * capture or CUDA graph, where cudaMalloc/cudaFree are not allowed; loops
+ * with hard latency limits, since cudaMalloc/cudaFree can synchronise the
+ * device; plugins whose host framework owns all GPU memory) and so cannot
+ * create a hydro_ctx.
+ *   U          device, FP64 [4][ny][nx] (rho, rho*u, rho*v, E), x fastest
+ *   nx, ny     >= 1; ny <= 32768 (larger ny returns HYDRO_EINVAL)
+ *   h          cell size (> 0)
+ *   sums       device, 4 doubles, written with the totals
+ *   cuda_stream  stream to enqueue on (NULL: the legacy default stream)
+ * Asynchronous on the stream; same summation order, hence the same bits, as
+ * hydro_conservation on an FP64 context holding the same state.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine: the per-row partial
+ * sums live in a fixed 1 MiB device array that every GPU loading the library
+ * keeps until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress, with the device current);
+ * make that first call before any stream capture.  Every call shares the
+ * array (each call overwrites the rows it uses), so calls that overlap on
+ * the GPU -- on different streams, or from several threads -- race.
+ * Returns HYDRO_EINVAL for null pointers or bad sizes, HYDRO_ECUDA if the
+ * device or the launch fails.  hydro_last_error does not report on it. */
+hydro_status hydro_conservation_noalloc(const double *U, int nx, int ny, double h, double *sums,
+                                        void *cuda_stream);
+
 /* Device counters (see hydro_stats). */
 hydro_status hydro_get_stats(hydro_ctx *ctx, hydro_stats *out);
 

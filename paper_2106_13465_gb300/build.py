@@ -20,7 +20,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # per-file extra flags: the FP32 sweep uses fast single-precision division,
 # square root and power (FP64 operations stay IEEE)
 EXTRA = {"sweep_f32.cu": ["--use_fast_math"]}
-SOURCES = ["hydro_abi.cu", "aux.cu", "sweep_f64.cu", "sweep_f32.cu"]
+SOURCES = ["hydro_abi.cu", "aux.cu", "sweep_f64.cu", "sweep_f32.cu", "noalloc.cu"]
 HEADERS = ["godunov.cuh", "kernels.h", "sweep_tma.cuh"]
 
 

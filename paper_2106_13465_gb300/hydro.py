@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "HYDRO_OK", 1: "HYDRO_EINVAL", 2: "HYDRO_ENOMEM", 3: "HYDRO_E
 EXPORTS = ("hydro_init", "hydro_destroy", "hydro_set_tuning", "hydro_set_state",
            "hydro_get_state", "hydro_step", "hydro_step_dt", "hydro_step_profiled", "hydro_cfl_dt", "hydro_get_time",
            "hydro_get_step", "hydro_set_step", "hydro_set_time",
-           "hydro_conservation", "hydro_get_stats", "hydro_last_error", "hydro_version")
+           "hydro_conservation", "hydro_conservation_noalloc", "hydro_get_stats",
+           "hydro_last_error", "hydro_version")
 
 
 class hydro_grid(ctypes.Structure):
@@ -88,6 +89,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.hydro_set_step.argtypes = [vp, ctypes.c_longlong]
     L.hydro_set_time.argtypes = [vp, ctypes.c_int, ctypes.c_double]
     L.hydro_conservation.argtypes = [vp, ctypes.c_int, D]
+    L.hydro_conservation_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp]
+    L.hydro_conservation_noalloc.restype = ctypes.c_int
     L.hydro_get_stats.argtypes = [vp, P(hydro_stats)]
     L.hydro_last_error.argtypes = [vp]
     L.hydro_last_error.restype = ctypes.c_char_p
@@ -174,6 +177,14 @@ def hydro_set_time(ctx, grid: int, t: float) -> int:
 def hydro_conservation(ctx, grid: int):
     s = np.zeros(4)
     return load().hydro_conservation(ctx, grid, _dptr(s)), s
+
+
+def hydro_conservation_noalloc(U_ptr: int, nx: int, ny: int, h: float, sums_ptr: int,
+                               stream: int | None = None) -> int:
+    """Totals of a device state [4, ny, nx] into a device array of 4 doubles,
+    without allocating (see include/hydro.h)."""
+    return load().hydro_conservation_noalloc(ctypes.c_void_p(U_ptr), nx, ny, h,
+                                             ctypes.c_void_p(sums_ptr), ctypes.c_void_p(stream or 0))
 
 
 def hydro_get_stats(ctx):
