@@ -85,17 +85,20 @@ typedef struct {
     void *cuda_stream;
 } hydro_params;
 
-/* Launch shape of the sweep kernels (all fields 0 = library default).
- *   tile_len      cells per tile along the sweep line (a multiple of 4); 0
- *                 chooses it per direction from a list-scheduling model of
- *                 the tile queue
- *   ctas_per_sm   resident CTAs per SM of the persistent sweep launch
+/* Launch shape of the sweep kernels (0 = library default / automatic).
+ *   tile_len      y sweep: rows per tile of 32 columns (a multiple of 4)
+ *   ctas_per_sm   resident CTAs per SM of the persistent sweep launches
+ *                 (at most the occupancy limit)
  *   graph_steps   steps captured per CUDA graph (even, 0 = no graph)
- * Results are bit-identical for every admissible setting. */
+ *   span_len      x sweep: cells of a row per warp task (a multiple of 64)
+ * tile_len and span_len default to the best makespan of a list-scheduling
+ * model of the tile queue on the resident warps.  Results are bit-identical
+ * for every admissible setting. */
 typedef struct {
     int tile_len;
     int ctas_per_sm;
     int graph_steps;
+    int span_len;
 } hydro_tuning;
 
 /* Counters kept on the device since hydro_init (hydro_stats()).

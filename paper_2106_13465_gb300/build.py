@@ -16,10 +16,12 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhydro.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-# per-file extra flags: the FP32 sweep uses fast single-precision division,
-# square root and power (FP64 operations stay IEEE)
-EXTRA = {"sweep_f32.cu": ["--use_fast_math"]}
+# no automatic multiply-add contraction: the kernels write every fused
+# multiply-add out, so all inlined copies of the arithmetic round alike
+COMMON = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# per-file extra flags: the FP32 sweep uses approximate single-precision
+# division and square root with denormals flushed (FP64 operations stay IEEE)
+EXTRA = {"sweep_f32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
 SOURCES = ["hydro_abi.cu", "aux.cu", "sweep_f64.cu", "sweep_f32.cu", "noalloc.cu"]
 HEADERS = ["godunov.cuh", "kernels.h", "sweep_tma.cuh"]
 

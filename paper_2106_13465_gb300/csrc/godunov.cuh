@@ -8,8 +8,11 @@
 //                  the PVRS guess), sampled at x/t = 0, physical flux there
 //
 // Everything here is a pure function of its arguments, so a cell's update
-// depends only on the cells i-2..i+2 of its line whatever the thread mapping:
-// results are identical for every tile shape and schedule.
+// depends only on the cells i-2..i+2 of its line whatever the thread mapping.
+// The kernels are built without automatic multiply-add contraction and every
+// fused multiply-add is written out (tfma), so each inlined copy of these
+// functions rounds identically: results are bit-identical for every tile
+// shape, schedule, sweep direction and kernel variant.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -53,6 +56,8 @@ __device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double tabs(double x) { return fabs(x); }
 __device__ __forceinline__ float tabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
 
 // x^e with the exact value 1 for x == 1 (pow(1, e) = 1 for every e).
 template <class T>
@@ -69,7 +74,8 @@ __device__ __forceinline__ Prim<T> cons_to_prim(const Consts<T>& K, const Cons<T
     ir = T(1) / W.r;
     W.u = U.mn * ir;
     W.v = U.mt * ir;
-    T p = K.gm1 * (U.E - T(0.5) * W.r * (W.u * W.u + W.v * W.v));
+    const T q2 = tfma(W.u, W.u, W.v * W.v);
+    T p = K.gm1 * tfma(T(-0.5) * W.r, q2, U.E);
     const T pm = W.r * K.cf2g;
     W.p = (p < pm) ? pm : p;
     return W;
@@ -106,18 +112,18 @@ __device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) *
     const T Du = minmod(W0.u - Wm.u, Wp.u - W0.u);
     const T Dv = minmod(W0.v - Wm.v, Wp.v - W0.v);
     const T Dp = minmod(W0.p - Wm.p, Wp.p - W0.p);
-    const T dr = hdtdx * (W0.u * Dr + W0.r * Du);
-    const T du = hdtdx * (W0.u * Du + Dp * ir0);
+    const T dr = hdtdx * tfma(W0.u, Dr, W0.r * Du);
+    const T du = hdtdx * tfma(W0.u, Du, Dp * ir0);
     const T dv = hdtdx * (W0.u * Dv);
-    const T dp = hdtdx * (K.gamma * W0.p * Du + W0.u * Dp);
-    WL.r = W0.r - T(0.5) * Dr + dr;
-    WL.u = W0.u - T(0.5) * Du + du;
-    WL.v = W0.v - T(0.5) * Dv + dv;
-    WL.p = W0.p - T(0.5) * Dp + dp;
-    WR.r = W0.r + T(0.5) * Dr + dr;
-    WR.u = W0.u + T(0.5) * Du + du;
-    WR.v = W0.v + T(0.5) * Dv + dv;
-    WR.p = W0.p + T(0.5) * Dp + dp;
+    const T dp = hdtdx * tfma(K.gamma * W0.p, Du, W0.u * Dp);
+    WL.r = tfma(T(-0.5), Dr, W0.r) + dr;
+    WL.u = tfma(T(-0.5), Du, W0.u) + du;
+    WL.v = tfma(T(-0.5), Dv, W0.v) + dv;
+    WL.p = tfma(T(-0.5), Dp, W0.p) + dp;
+    WR.r = tfma(T(0.5), Dr, W0.r) + dr;
+    WR.u = tfma(T(0.5), Du, W0.u) + du;
+    WR.v = tfma(T(0.5), Dv, W0.v) + dv;
+    WR.p = tfma(T(0.5), Dp, W0.p) + dp;
     WL.r = (WL.r < K.rho_floor) ? K.rho_floor : WL.r;
     WR.r = (WR.r < K.rho_floor) ? K.rho_floor : WR.r;
     const T pml = WL.r * K.cf2g, pmr = WR.r * K.cf2g;
@@ -179,13 +185,13 @@ __device__ __forceinline__ void pressure_fn(const Consts<T>& K, const Side<T>& s
         const T dpk = p - s.p;
         f = dpk * q;
         a = T(0);
-        b = q * (T(1) - T(0.5) * dpk * (q * q * s.iA));
+        b = q * tfma(T(-0.5) * dpk, q * q * s.iA, T(1));
         pz = T(-1);
     } else {
         const bool one = (p == s.p);
         const T r = one ? T(1) : p * s.ip;
         pz = one ? T(1) : tpow(r, K.z);
-        f = s.cG4 * (pz - T(1));
+        f = tfma(s.cG4, pz, -s.cG4);
         a = pz * s.irc * s.p;
         b = T(0);
     }
@@ -209,7 +215,7 @@ struct Star {
 template <class T>
 __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T>& L,
                                                 const Side<T>& R) {
-    T p = T(0.5) * (L.p + R.p) - T(0.125) * (R.u - L.u) * (L.r + R.r) * (L.c + R.c);
+    T p = tfma(T(-0.125) * (R.u - L.u), (L.r + R.r) * (L.c + R.c), T(0.5) * (L.p + R.p));
     bool floored = false;
     if (p < K.pmin) { p = K.pmin; floored = true; }
     const T du = R.u - L.u;
@@ -219,16 +225,16 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
         pressure_fn(K, L, p, fl, al, bl, pzl);
         pressure_fn(K, R, p, fr, ar, br, pzr);
         const T F = fl + fr + du;
-        const T g = F / ((al + ar) + p * (bl + br));   // Newton step / p
+        const T g = F / tfma(p, bl + br, al + ar);     // Newton step / p
         T d = g * p;                                    // the step p - p_new
         T pn = p - d;
         T rel = g;                                      // d / p
         if (pn < K.pmin) { pn = K.pmin; floored = true; d = p - pn; rel = d / p; }
         if (tabs(d) <= K.tol * pn) {
-            fl -= al * rel + bl * d;
-            fr -= ar * rel + br * d;
-            if (pzl > T(0)) pzl -= K.z * pzl * rel;
-            if (pzr > T(0)) pzr -= K.z * pzr * rel;
+            fl -= tfma(al, rel, bl * d);
+            fr -= tfma(ar, rel, br * d);
+            if (pzl > T(0)) pzl = tfma(-K.z * pzl, rel, pzl);
+            if (pzr > T(0)) pzr = tfma(-K.z * pzr, rel, pzr);
             p = pn;
             conv = true;
             break;
@@ -241,7 +247,7 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
     }
     Star<T> st;
     st.p = p;
-    st.u = T(0.5) * (L.u + R.u) + T(0.5) * (fr - fl);
+    st.u = tfma(T(0.5), fr - fl, T(0.5) * (L.u + R.u));
     st.pzl = pzl;
     st.pzr = pzr;
     st.floored = floored;
@@ -265,20 +271,20 @@ __device__ __forceinline__ Prim<T> sample_side(const Consts<T>& K, const Side<T>
     const bool one = (st.p == S.p);
     const T pr = one ? T(1) : st.p * S.ip;
     if (st.p > S.p) {
-        const T sk = sgn * S.u - S.c * tsqrt(K.zs * pr + K.z);   // = sgn * S_K
+        const T sk = tfma(-S.c, tsqrt(tfma(K.zs, pr, K.z)), sgn * S.u);   // = sgn * S_K
         if (T(0) <= sk) { W.r = S.r; W.u = S.u; W.p = S.p; }
-        else { W.r = S.r * (pr + K.G6) / (K.G6 * pr + T(1)); W.u = st.u; W.p = st.p; }
+        else { W.r = S.r * (pr + K.G6) / tfma(K.G6, pr, T(1)); W.u = st.u; W.p = st.p; }
     } else {
         const T hk = sgn * S.u - S.c;                              // head
         if (T(0) <= hk) { W.r = S.r; W.u = S.u; W.p = S.p; }
         else {
             if (pz < T(0)) pz = one ? T(1) : tpow(pr, K.z);
-            const T tk = sgn * st.u - S.c * pz;                    // tail
+            const T tk = tfma(-S.c, pz, sgn * st.u);               // tail
             if (T(0) > tk) {
                 W.r = one ? S.r : S.r * pr / (pz * pz);
                 W.u = st.u; W.p = st.p;
             } else {
-                const T c = K.G5 * (S.c + sgn * K.G7 * S.u);
+                const T c = K.G5 * tfma(sgn * K.G7, S.u, S.c);
                 const T cc = c / S.c;
                 W.u = sgn * c;
                 W.r = S.r * tpow(cc, K.G4);
@@ -299,11 +305,12 @@ __device__ __forceinline__ Prim<T> sample0(const Consts<T>& K, const Side<T>& L,
 // Physical flux along the normal of a primitive state.
 template <class T>
 __device__ __forceinline__ Cons<T> physical_flux(const Consts<T>& K, const Prim<T>& W) {
-    const T E = W.p * K.inv_gm1 + T(0.5) * W.r * (W.u * W.u + W.v * W.v);
+    const T q2 = tfma(W.u, W.u, W.v * W.v);
+    const T E = tfma(T(0.5) * W.r, q2, W.p * K.inv_gm1);
     const T m = W.r * W.u;
     Cons<T> F;
     F.r = m;
-    F.mn = m * W.u + W.p;
+    F.mn = tfma(m, W.u, W.p);
     F.mt = m * W.v;
     F.E = W.u * (E + W.p);
     return F;

@@ -86,7 +86,7 @@ struct hydro_ctx {
     int* d_redo = nullptr;          // [2][redo_cap] FP32 second-pass tile lists
     int redo_cap = 0;
     int ctas_redo[2] = {0, 0};
-    hydro_tuning tuning{kDefaultTileLen, 0, kDefaultGraphSteps};
+    hydro_tuning tuning{kDefaultTileLen, 0, kDefaultGraphSteps, 0};
     int ctas[2] = {0, 0};       // CTAs per sweep launch (x, y)
     int tile_len_used[2] = {0, 0};
     long long step = 0;         // steps since the last hydro_set_state
@@ -154,29 +154,41 @@ hydro_status validate_params(const hydro_params* p) {
     return HYDRO_OK;
 }
 
-// Tile work-lists: for each grid, lines in groups of 32 (one per lane),
-// cells along the line in segments of tile_len.
-void build_tiles(const std::vector<GridDesc>& gd, int dir, int tile_len, std::vector<Tile>& out) {
+// Tile work-lists.  y sweep: for each grid, columns in groups of 32 (one per
+// lane), rows in segments of len.  x sweep: for each grid and row, spans of
+// len cells (one warp task each).
+void build_tiles(const std::vector<GridDesc>& gd, int dir, int len, std::vector<Tile>& out) {
     out.clear();
     for (int g = 0; g < (int)gd.size(); ++g) {
-        const int nlines = dir == DIR_X ? gd[g].ny : gd[g].nx;
-        const int n = dir == DIR_X ? gd[g].nx : gd[g].ny;
-        for (int l0 = 0; l0 < nlines; l0 += kWarpLines)
-            for (int c0 = 0; c0 < n; c0 += tile_len)
-                out.push_back(Tile{g, l0, c0, std::min(tile_len, n - c0)});
+        if (dir == DIR_Y) {
+            for (int l0 = 0; l0 < gd[g].nx; l0 += kWarpLines)
+                for (int c0 = 0; c0 < gd[g].ny; c0 += len)
+                    out.push_back(Tile{g, l0, c0, std::min(len, gd[g].ny - c0)});
+        } else {
+            for (int j = 0; j < gd[g].ny; ++j)
+                for (int c0 = 0; c0 < gd[g].nx; c0 += len)
+                    out.push_back(Tile{g, j, c0, std::min(len, gd[g].nx - c0)});
+        }
     }
 }
 
+// Cost of a tile in cell units for the scheduling model: y, its cells plus
+// its 4-cell halo; x, the 64-cell segments its warp walks (one more than its
+// length needs) plus a fixed start-up.
+double tile_cost(const Tile& t, int dir) {
+    if (dir == DIR_Y) return t.ncell + 4.0;
+    return ((t.ncell + 1) / kXSegment + 1) * (double)kXSegment + 16.0;
+}
+
 // Makespan of the dynamic tile queue on `warps` resident warps (list
-// scheduling in queue order), a tile of ncell cells costing ncell + 4 cell
-// units (its halo: two extra reads, one extra trace and interface solve).
-double list_schedule_makespan(const std::vector<Tile>& tiles, int warps) {
+// scheduling in queue order).
+double list_schedule_makespan(const std::vector<Tile>& tiles, int dir, int warps) {
     std::vector<double> heap(std::max(1, warps), 0.0);  // min-heap of warp finish times
     std::make_heap(heap.begin(), heap.end(), std::greater<double>());
     double span = 0.0;
     for (const Tile& t : tiles) {
         std::pop_heap(heap.begin(), heap.end(), std::greater<double>());
-        heap.back() += t.ncell + 4.0;
+        heap.back() += tile_cost(t, dir);
         span = std::max(span, heap.back());
         std::push_heap(heap.begin(), heap.end(), std::greater<double>());
     }
@@ -185,14 +197,19 @@ double list_schedule_makespan(const std::vector<Tile>& tiles, int warps) {
 
 int auto_tile_len(const std::vector<GridDesc>& gd, int dir, int warps) {
     std::vector<int> cand;
-    for (int L = 16; L <= 128; L += 4) cand.push_back(L);
-    for (int L : {160, 192, 256, 384, 512}) cand.push_back(L);
-    int best = 64;
+    if (dir == DIR_Y) {
+        for (int L = 16; L <= 128; L += 4) cand.push_back(L);
+        for (int L : {160, 192, 256, 384, 512}) cand.push_back(L);
+    } else {
+        for (int L : {64, 128, 192, 256, 320, 384, 512, 640, 768, 1024, 1536, 2048, 4096}) cand.push_back(L);
+    }
+    int best = cand[0];
     double best_span = 1e300;
     std::vector<Tile> t;
     for (int L : cand) {
         build_tiles(gd, dir, L, t);
-        const double span = list_schedule_makespan(t, warps);
+        if (t.size() > 4000000) continue;
+        const double span = list_schedule_makespan(t, dir, warps);
         if (span < best_span * 0.999) { best_span = span; best = L; }
     }
     return best;
@@ -209,7 +226,6 @@ hydro_status build_tensor_maps(hydro_ctx* c) {
     const size_t nmaps = c->gd.size() * 4;
     std::vector<CUtensorMap> maps(nmaps);
     const CUtensorMapDataType dtype = c->prec == 64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const cuuint32_t cx = (cuuint32_t)(16 / c->esz);
     for (size_t g = 0; g < c->gd.size(); ++g) {
         const GridDesc& d = c->gd[g];
         const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, 4};
@@ -218,7 +234,7 @@ hydro_status build_tensor_maps(hydro_ctx* c) {
         for (int b = 0; b < 2; ++b) {
             void* base = (char*)c->buf[b] + (size_t)d.off * c->esz;
             for (int dir = 0; dir < 2; ++dir) {
-                const cuuint32_t box[3] = {dir == DIR_X ? cx : 32u, dir == DIR_X ? 32u : 4u, 4u};
+                const cuuint32_t box[3] = {dir == DIR_X ? (cuuint32_t)kXSegment : 32u, dir == DIR_X ? 1u : 4u, 4u};
                 CUresult r = encode(&maps[(g * 2 + b) * 2 + dir], dtype, 3, base, dims, strides, box, estr,
                                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -244,7 +260,8 @@ hydro_status upload_tiles(hydro_ctx* c) {
         if (per_sm <= 0 || per_sm > occ) per_sm = occ;
         const int warps_per_cta = kSweepThreads / 32;
         const int resident_warps = c->nsm * per_sm * warps_per_cta;
-        const int L = c->tuning.tile_len > 0 ? c->tuning.tile_len : auto_tile_len(c->gd, d, resident_warps);
+        const int chosen = d == DIR_X ? c->tuning.span_len : c->tuning.tile_len;
+        const int L = chosen > 0 ? chosen : auto_tile_len(c->gd, d, resident_warps);
         c->tile_len_used[d] = L;
         std::vector<Tile> t;
         build_tiles(c->gd, d, L, t);
@@ -502,6 +519,8 @@ hydro_status hydro_set_tuning(hydro_ctx* c, const hydro_tuning* t) {
     hydro_tuning n = *t;
     if (n.tile_len != 0 && (n.tile_len < 4 || n.tile_len > (1 << 24) || (n.tile_len & 3)))
         return fail(c, HYDRO_EINVAL, "tile_len must be 0 (automatic) or a multiple of 4 in [4, 2^24]");
+    if (n.span_len != 0 && (n.span_len < kXSegment || n.span_len > (1 << 24) || (n.span_len % kXSegment)))
+        return fail(c, HYDRO_EINVAL, "span_len must be 0 (automatic) or a multiple of 64 in [64, 2^24]");
     if (n.ctas_per_sm < 0 || n.ctas_per_sm > 64) return fail(c, HYDRO_EINVAL, "ctas_per_sm must be in [0, 64]");
     if (n.graph_steps < 0 || (n.graph_steps & 1) || n.graph_steps > 1000)
         return fail(c, HYDRO_EINVAL, "graph_steps must be even and in [0, 1000]");

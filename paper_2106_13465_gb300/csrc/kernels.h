@@ -14,9 +14,13 @@
 // Each grid and buffer also has two TMA tensor maps over this layout, a 3D
 // tensor (x, y, q) of extents (nx, ny, 4) with byte strides
 // (pitch * esz, plane * esz):
-//   x-sweep map: box (16 bytes of x, 32 rows, 4 planes)  -- 32 lines x C cells
-//   y-sweep map: box (32 columns, 4 rows, 4 planes)      -- 32 lines x 4 cells
+//   x-sweep map: box (64 cells, 1 row, 4 planes)    -- one row segment
+//   y-sweep map: box (32 columns, 4 rows, 4 planes) -- 32 columns x 4 cells
 // stored at maps[(grid * 2 + buffer) * 2 + dir].
+//
+// Work lists.  y sweep: a tile is 32 columns (one per lane) x ncell rows.
+// x sweep: a tile is one row x ncell cells (a warp walks it in 64-cell
+// segments), stored as (grid, line0 = row, cell0 = first x, ncell).
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -37,12 +41,14 @@ enum { VAR_F64 = 0, VAR_F32_MAIN = 1, VAR_F32_REDO = 2 };
 constexpr int kWarpLines = 32;      // lines per warp tile (one per lane)
 constexpr int kSweepThreads = 128;  // threads per CTA of the sweep kernels
 
-// cells per TMA chunk along the sweep line and ring depth per warp
+// TMA ring geometry per warp.  x sweep: one slot holds a 64-cell segment of
+// one row, 4 planes; y sweep: one slot holds 4 rows x 32 columns, 4 planes.
+constexpr int kXSegment = 64;
+__host__ __device__ constexpr int ring_slots(int dir) { return 4; }
 template <class T>
-__host__ __device__ constexpr int chunk_cells(int dir) { return dir == DIR_X ? 16 / (int)sizeof(T) : 4; }
-__host__ __device__ constexpr int ring_slots(int dir) { return dir == DIR_X ? 6 : 4; }
-template <class T>
-__host__ __device__ constexpr int slot_bytes(int dir) { return 4 * 32 * chunk_cells<T>(dir) * (int)sizeof(T); }
+__host__ __device__ constexpr int slot_bytes(int dir) {
+    return dir == DIR_X ? 4 * kXSegment * (int)sizeof(T) : 4 * 4 * 32 * (int)sizeof(T);
+}
 template <class T>
 __host__ __device__ constexpr int sweep_smem_bytes(int dir) {
     return (kSweepThreads / 32) * ring_slots(dir) * (slot_bytes<T>(dir) + 8);

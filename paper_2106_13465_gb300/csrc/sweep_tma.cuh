@@ -157,12 +157,15 @@ struct FluxOp<float, VAR_F32_REDO> {
     }
 };
 
-template <class T, int VAR>
-struct MinBlocks { static constexpr int value = 1; };
-template <> struct MinBlocks<float, VAR_F32_MAIN> { static constexpr int value = 4; };
-template <> struct MinBlocks<double, VAR_F64> { static constexpr int value = 2; };
 
 // ------------------------------------------------------------ helpers -----
+template <class T>
+__device__ __forceinline__ Cons<T> flip(Cons<T> u, bool f) {
+    if (f) u.mn = -u.mn;
+    return u;
+}
+
+// Cell k of a line straight from global memory (boundary cells, span halos).
 template <class T, int DIR>
 __device__ __forceinline__ Cons<T> global_cell(const T* __restrict__ base, const GridDesc& g, int line, int k) {
     constexpr int PN = (DIR == DIR_X) ? 1 : 2, PT = 3 - PN;
@@ -175,309 +178,277 @@ __device__ __forceinline__ Cons<T> global_cell(const T* __restrict__ base, const
     return u;
 }
 
-// this lane's cells of a chunk in shared memory (normal/tangential order)
+// The state at position k of a line of n cells when k is outside [0, n):
+// mirror image (reflective: normal momentum negated; transmissive) or
+// wrap-around (periodic).
 template <class T, int DIR>
-__device__ __forceinline__ void read_chunk(const unsigned char* slot, int lane, Cons<T> (&cell)[chunk_cells<T>(DIR)]) {
-    constexpr int C = chunk_cells<T>(DIR);
-    constexpr int PB = 32 * C * (int)sizeof(T);  // bytes per plane
-    constexpr int PN = (DIR == DIR_X) ? 1 : 2, PT = 3 - PN;
-    if (DIR == DIR_X) {
-        // one 16-byte row per plane: C consecutive cells of this lane's row
-        T v[4][C];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 raw = *reinterpret_cast<const float4*>(slot + q * PB + lane * 16);
-            const T* e = reinterpret_cast<const T*>(&raw);
-#pragma unroll
-            for (int j = 0; j < C; ++j) v[q][j] = e[j];
+__device__ __forceinline__ Cons<T> ghost_cell(const T* __restrict__ base, const GridDesc& g, int line, int k,
+                                              int n, int bclo, int bchi) {
+    const int bc = (k < 0) ? bclo : bchi;
+    if (bc == BC_PERIODIC) return global_cell<T, DIR>(base, g, line, (k < 0) ? k + n : k - n);
+    return flip(global_cell<T, DIR>(base, g, line, (k < 0) ? -1 - k : 2 * n - 1 - k), bc == BC_REFLECT);
+}
+
+// Per-warp ring of TMA slots with one mbarrier each.
+template <int S, int SLOT>
+struct WarpRing {
+    unsigned char* base;
+    uint64_t* bar;
+    unsigned parity = 0;   // bit s: parity of the next completion of slot s
+    unsigned pending = 0;  // bit s: a load into slot s is in flight (lane 0's view)
+
+    __device__ __forceinline__ void init(unsigned char* smem, int warp, int nwarps, int lane) {
+        base = smem + warp * S * SLOT;
+        bar = reinterpret_cast<uint64_t*>(smem + nwarps * S * SLOT) + warp * S;
+        if (lane == 0) {
+            for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+            fence_mbar_init();
         }
-#pragma unroll
-        for (int j = 0; j < C; ++j) cell[j] = Cons<T>{v[0][j], v[PN][j], v[PT][j], v[3][j]};
-    } else {
-        const T* s = reinterpret_cast<const T*>(slot);
-#pragma unroll
-        for (int j = 0; j < C; ++j)
-            cell[j] = Cons<T>{s[(0 * C + j) * 32 + lane], s[(PN * C + j) * 32 + lane],
-                              s[(PT * C + j) * 32 + lane], s[(3 * C + j) * 32 + lane]};
+        __syncwarp();
+    }
+    __device__ __forceinline__ unsigned char* slot(int s) const { return base + s * SLOT; }
+    // lane 0: load box (x, y, 0) of `map` into slot s
+    __device__ __forceinline__ void issue(int s, const CUtensorMap* map, int x, int y) {
+        mbar_expect_tx(&bar[s], SLOT);
+        tma_load_3d(base + s * SLOT, map, x, y, 0, &bar[s]);
+        pending |= 1u << s;
+    }
+    // all lanes: wait for slot s (bounded; the verdict is warp-uniform)
+    __device__ __forceinline__ bool wait(int s, int lane) {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[s], (parity >> s) & 1u));
+        if (ok) {
+            parity ^= 1u << s;
+            if (lane == 0) pending &= ~(1u << s);
+        }
+        return ok;
+    }
+    // lane 0, after a timeout: wait (bounded) for this warp's copies in flight
+    __device__ __forceinline__ void drain() {
+        for (int s = 0; s < S; ++s)
+            if (pending & (1u << s)) mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
+    }
+};
+
+// Claim the next tile: the main pass takes the work list in order, the FP32
+// second pass takes the tiles the main pass queued.  -1 when none is left.
+template <class T, int VAR>
+__device__ __forceinline__ int claim_tile(const SweepArgs<T>& a, int lane) {
+    int t = 0;
+    if (lane == 0) {
+        if (VAR == VAR_F32_REDO) {
+            const unsigned i = atomicAdd(&a.ctr->redo_claim[a.which], 1u);
+            t = (i < a.ctr->redo_count[a.which]) ? a.redo_list[a.which * a.redo_cap + i] : -1;
+        } else {
+            const unsigned i = atomicAdd(&a.ctr->tile_ctr[a.which], 1u);
+            t = (i < (unsigned)a.ntiles) ? (int)i : -1;
+        }
+    }
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
+// End of a tile: an FP32 main-pass tile with a near-vacuum interface is queued
+// for the second pass (its results there replace these); otherwise its status
+// bits and, on the second sweep of a step, its wave-speed maximum are kept.
+template <class T, int VAR, int WHICH>
+__device__ __forceinline__ void finish_tile(const SweepArgs<T>& a, int t, int grid, unsigned acc, bool redo,
+                                            unsigned tbad, T smax, unsigned& kbad, int lane) {
+    if (VAR == VAR_F32_MAIN && __any_sync(0xffffffffu, redo)) {
+        if (lane == 0) {
+            const unsigned i = atomicAdd(&a.ctr->redo_count[a.which], 1u);
+            a.redo_list[a.which * a.redo_cap + i] = t;
+        }
+        return;
+    }
+    kbad |= tbad;
+    if (WHICH == 1) {
+        double m = (double)smax;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v = __shfl_xor_sync(0xffffffffu, m, o);
+            m = (v <= m) ? m : v;
+        }
+        if (lane == 0) atomicMax(&a.run[grid].wmax[acc], (unsigned long long)__double_as_longlong(m));
     }
 }
 
-// write this lane's result for cell j of a chunk (x sweep, in place)
-template <class T>
-__device__ __forceinline__ void write_slot_x(unsigned char* slot, int lane, int j, const Cons<T>& u) {
-    constexpr int C = chunk_cells<T>(DIR_X);
-    constexpr int PB = 32 * C * (int)sizeof(T);
-    T* p = reinterpret_cast<T*>(slot + lane * 16) + j;
-    *p = u.r;
-    *reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(p) + 1 * PB) = u.mn;
-    *reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(p) + 2 * PB) = u.mt;
-    *reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(p) + 3 * PB) = u.E;
+// Status bits and (second sweep) CFL wave speed of one new cell state.
+template <class T, int WHICH>
+__device__ __forceinline__ void check_cell(const Consts<T>& K, const Cons<T>& out, unsigned& tbad, T& smax) {
+    tbad |= (out.r > T(0)) ? 0u : STATUS_BAD_RHO;
+    tbad |= (out.E > T(0)) ? 0u : STATUS_BAD_E;
+    if (WHICH == 1) {
+        T ir;
+        const Prim<T> w = cons_to_prim(K, out, ir);
+        const T au = tabs(w.u), av = tabs(w.v);
+        const T sp = ((au > av) ? au : av) + tsqrt(K.gamma * w.p * ir);
+        smax = (sp <= smax) ? smax : sp;
+    }
 }
 
 template <class T>
-__device__ __forceinline__ Cons<T> flip(Cons<T> u, bool f) {
-    if (f) u.mn = -u.mn;
-    return u;
+__device__ __forceinline__ Cons<T> update(const Cons<T>& u, T dtdx, const Cons<T>& fhi, const Cons<T>& flo) {
+    Cons<T> o;
+    o.r = tfma(-dtdx, fhi.r - flo.r, u.r);
+    o.mn = tfma(-dtdx, fhi.mn - flo.mn, u.mn);
+    o.mt = tfma(-dtdx, fhi.mt - flo.mt, u.mt);
+    o.E = tfma(-dtdx, fhi.E - flo.E, u.E);
+    return o;
 }
 
-// --------------------------------------------------------------- kernel ---
-template <class T, int DIR, int VAR>
-__global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR>::value))
-    sweep_kernel(const SweepArgs<T> a) {
-    constexpr int C = chunk_cells<T>(DIR);
-    constexpr int S = ring_slots(DIR);
-    constexpr int SLOT = slot_bytes<T>(DIR);
-    constexpr int PN = (DIR == DIR_X) ? 1 : 2, PT = 3 - PN;
-    constexpr int SKIP = (DIR == DIR_X && sizeof(T) == 4) ? 2 : 0;  // x FP32: 4-cell aligned halo
+template <class T, int VAR, int DIR>
+struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_Y> { static constexpr int value = 4; };
+template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_X> { static constexpr int value = 4; };
+template <> struct MinBlocks<double, VAR_F64, DIR_Y> { static constexpr int value = 2; };
+template <> struct MinBlocks<double, VAR_F64, DIR_X> { static constexpr int value = 2; };
+
+// =================================================================== y ===
+// Lines are columns: lane l walks column line0 + l down a tile of rows
+// [s0, s1), with 4-row chunks (rows s0-2+4c .. s0+1+4c) arriving by TMA.
+// Chunk 0 holds the four warm-up positions s0-2 .. s0+1; every later chunk
+// holds four positions that each complete one output row.
+template <class T>
+struct YWalk {
+    Cons<T> u0, u1;   // conserved states at k-2, k-1
+    Prim<T> w0, w1;   // primitives at k-2, k-1
+    T ir1;            // 1/rho at k-1
+    Prim<T> wr0;      // right face of cell k-2
+    Cons<T> flo;      // flux at (k-2) - 1/2
+};
+
+template <class T, int VAR, int WHICH>
+__device__ __forceinline__ void y_step(const SweepArgs<T>& a, YWalk<T>& s, const Cons<T>& u, T dtdx, T hdtdx,
+                                       bool& redo, unsigned& nfb, T* __restrict__ d, long long plane, bool valid,
+                                       unsigned& tbad, T& smax) {
+    // position k arrives: trace cell k-1, solve interface k-2 | k-1, update cell k-2
+    constexpr int PN = 2, PT = 1;
+    T ir2;
+    const Prim<T> w2 = cons_to_prim(a.K, u, ir2);
+    Prim<T> wl1, wr1;
+    trace(a.K, hdtdx, s.w0, s.w1, s.ir1, w2, wl1, wr1);
+    const Cons<T> fhi = FluxOp<T, VAR>::eval(a, s.wr0, wl1, redo, nfb);
+    const Cons<T> out = update(s.u0, dtdx, fhi, s.flo);
+    if (valid) {
+        d[0] = out.r;
+        d[PN * plane] = out.mn;
+        d[PT * plane] = out.mt;
+        d[3 * plane] = out.E;
+        check_cell<T, WHICH>(a.K, out, tbad, smax);
+    }
+    s.flo = fhi;
+    s.u0 = s.u1; s.u1 = u;
+    s.w0 = s.w1; s.w1 = w2; s.ir1 = ir2;
+    s.wr0 = wr1;
+}
+
+template <class T, int VAR, int WHICH>
+__global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::value))
+    sweep_y_kernel(const SweepArgs<T> a) {
+    constexpr int C = 4;
+    constexpr int S = ring_slots(DIR_Y);
+    constexpr int SLOT = slot_bytes<T>(DIR_Y);
     constexpr int NWARPS = kSweepThreads / 32;
-
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* ring = smem + warp * S * SLOT;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NWARPS * S * SLOT) + warp * S;
-    if (lane == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
+    WarpRing<S, SLOT> ring;
+    ring.init(smem, warp, NWARPS, lane);
 
     const Consts<T>& K = a.K;
     const unsigned acc = a.ctr->acc;
-    unsigned parity = 0;   // bit s: parity of the next completion of slot s
-    unsigned pending = 0;  // bit s: a load into slot s is in flight (lane 0's view)
     unsigned kbad = 0, nfb = 0;
     bool aborted = false;
 
     for (;;) {
-        // ---- claim a tile ------------------------------------------------
-        int t = 0;
-        if (lane == 0) {
-            if (VAR == VAR_F32_REDO) {
-                const unsigned i = atomicAdd(&a.ctr->redo_claim[a.which], 1u);
-                t = (i < a.ctr->redo_count[a.which]) ? a.redo_list[a.which * a.redo_cap + i] : -1;
-            } else {
-                const unsigned i = atomicAdd(&a.ctr->tile_ctr[a.which], 1u);
-                t = (i < (unsigned)a.ntiles) ? (int)i : -1;
-            }
-        }
-        t = __shfl_sync(0xffffffffu, t, 0);
+        const int t = claim_tile<T, VAR>(a, lane);
         if (t < 0) break;
-
         const Tile tile = a.tiles[t];
         const GridDesc g = a.grids[tile.grid];
         const double dt = a.run[tile.grid].dt;
-        const int n = (DIR == DIR_X) ? g.nx : g.ny;
-        const int nlines = (DIR == DIR_X) ? g.ny : g.nx;
+        const int n = g.ny, nlines = g.nx;
         const int line0 = tile.line0, line = line0 + lane;
         const bool valid = line < nlines;
-        const int bclo = (DIR == DIR_X) ? g.bc[0] : g.bc[2];
-        const int bchi = (DIR == DIR_X) ? g.bc[1] : g.bc[3];
-        const int s0 = tile.cell0, s1 = tile.cell0 + tile.ncell;
-        const int kfirst = s0 - 2 - SKIP;  // first position of chunk 0
-        const int klast = s1 + 1;          // last position the walk needs
-        const int nch = (klast - kfirst) / C + 1;
-        const CUtensorMap* msrc = a.maps + ((size_t)tile.grid * 2 + a.src_buf) * 2 + DIR;
-        const CUtensorMap* mdst = a.maps + ((size_t)tile.grid * 2 + (a.src_buf ^ 1)) * 2 + DIR;
-
-        auto issue = [&](int c) {  // lane 0
-            const int s = c % S;
-            mbar_expect_tx(&bar[s], SLOT);
-            if (DIR == DIR_X) tma_load_3d(ring + s * SLOT, msrc, kfirst + c * C, line0, 0, &bar[s]);
-            else tma_load_3d(ring + s * SLOT, msrc, line0, kfirst + c * C, 0, &bar[s]);
-            pending |= 1u << s;
-        };
-        if (lane == 0)
-            for (int c = 0; c < S && c < nch; ++c) issue(c);
-
-        // ---- ghosts at the low end of the line ------------------------------
-        Cons<T> gl0 = {T(1), T(0), T(0), T(1)}, gl1 = gl0;  // positions -2, -1
         const int lsafe = valid ? line : nlines - 1;
-        if (s0 == 0) {
-            if (bclo == BC_PERIODIC) {
-                gl0 = global_cell<T, DIR>(a.src, g, lsafe, n - 2);
-                gl1 = global_cell<T, DIR>(a.src, g, lsafe, n - 1);
-            } else {
-                // mirror of cells 1 and 0, which sit in one chunk of the ring
-                const int c0 = (0 - kfirst) / C, j0 = (0 - kfirst) % C;
-                const int s = c0 % S;
-                if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[s], (parity >> s) & 1u))) {
-                    aborted = true;
-                    break;
-                }
-                Cons<T> cell[C];
-                read_chunk<T, DIR>(ring + s * SLOT, lane, cell);
-                const bool f = (bclo == BC_REFLECT);
-                gl1 = flip(cell[j0], f);
-                gl0 = flip(cell[j0 + 1], f);
-            }
-        }
+        const int bclo = g.bc[2], bchi = g.bc[3];
+        const int s0 = tile.cell0, s1 = tile.cell0 + tile.ncell;
+        const int kfirst = s0 - 2, klast = s1 + 1;
+        const int nch = (klast - kfirst) / C + 1;
+        const CUtensorMap* msrc = a.maps + ((size_t)tile.grid * 2 + a.src_buf) * 2 + DIR_Y;
+        if (lane == 0)
+            for (int c = 0; c < S && c < nch; ++c) ring.issue(c, msrc, line0, kfirst + c * C);
 
-        // ---- walk ---------------------------------------------------------
         const T dtdx = T(dt / g.h);
         const T hdtdx = T(-0.5) * dtdx;
-        const bool fhi_flip = (bchi == BC_REFLECT);
-        Cons<T> u0 = gl0, u1 = gl0, grh = gl0;
-        Prim<T> w0 = {T(1), T(0), T(0), T(1)}, w1 = w0, wr0 = w0;
-        T ir1 = T(1);
-        Cons<T> flo = {T(0), T(0), T(0), T(0)};
+        T* __restrict__ dcol = a.dst + g.off + line;
+        YWalk<T> w;
         T smax = T(0);
         unsigned tbad = 0;
         bool redo = false;
 
         for (int c = 0; c < nch; ++c) {
-            const int s = c % S;
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[s], (parity >> s) & 1u))) {
-                aborted = true;
-                break;
-            }
-            parity ^= 1u << s;
-            if (lane == 0) pending &= ~(1u << s);
+            const int sl = c % S;
+            if (!ring.wait(sl, lane)) { aborted = true; break; }
+            const T* sp = reinterpret_cast<const T*>(ring.slot(sl));
             Cons<T> cell[C];
-            read_chunk<T, DIR>(ring + s * SLOT, lane, cell);
-
 #pragma unroll
-            for (int j = 0; j < C; ++j) {
-                const int k = kfirst + c * C + j;
-                if (k < s0 - 2 || k > klast) continue;  // warp-uniform
-                Cons<T> u = cell[j];
-                if (k < 0) {
-                    u = (k == -2) ? gl0 : gl1;
-                } else if (k >= n) {
-                    if (bchi == BC_PERIODIC) {
-                        u = global_cell<T, DIR>(a.src, g, lsafe, k - n);
-                    } else if (k == n) {
-                        u = flip(u1, fhi_flip);      // mirror of cell n-1
-                        grh = flip(u0, fhi_flip);    // mirror of cell n-2, for n+1
+            for (int j = 0; j < C; ++j)
+                cell[j] = Cons<T>{sp[(0 * C + j) * 32 + lane], sp[(2 * C + j) * 32 + lane],
+                                  sp[(1 * C + j) * 32 + lane], sp[(3 * C + j) * 32 + lane]};
+            const int kc = kfirst + c * C;
+            if (c > 0 && kc + C - 1 < n && kc + C - 1 <= klast) {
+                // steady state: four interior positions, each completes a row
+#pragma unroll
+                for (int j = 0; j < C; ++j)
+                    y_step<T, VAR, WHICH>(a, w, cell[j], dtdx, hdtdx, redo, nfb,
+                                          dcol + (long long)(kc + j - 2) * g.pitch, g.plane, valid, tbad, smax);
+            } else {
+                // warm-up chunk or a chunk reaching past the line or the tile
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    const int k = kc + j;
+                    if (k > klast) break;
+                    Cons<T> u = cell[j];
+                    if (k < 0 || k >= n) u = ghost_cell<T, DIR_Y>(a.src, g, lsafe, k, n, bclo, bchi);
+                    if (k == s0 - 2) {
+                        w.u0 = u;
+                        w.w0 = cons_to_prim(K, u);
+                    } else if (k == s0 - 1) {
+                        w.u1 = u;
+                        w.w1 = cons_to_prim(K, u, w.ir1);
+                    } else if (k == s0) {
+                        T ir2;
+                        const Prim<T> w2 = cons_to_prim(K, u, ir2);
+                        Prim<T> wl1;
+                        trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, w.wr0);
+                        w.u0 = w.u1; w.u1 = u;
+                        w.w0 = w.w1; w.w1 = w2; w.ir1 = ir2;
+                    } else if (k == s0 + 1) {
+                        T ir2;
+                        const Prim<T> w2 = cons_to_prim(K, u, ir2);
+                        Prim<T> wl1, wr1;
+                        trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);
+                        w.flo = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb);
+                        w.u0 = w.u1; w.u1 = u;
+                        w.w0 = w.w1; w.w1 = w2; w.ir1 = ir2;
+                        w.wr0 = wr1;
                     } else {
-                        u = grh;
+                        y_step<T, VAR, WHICH>(a, w, u, dtdx, hdtdx, redo, nfb,
+                                              dcol + (long long)(k - 2) * g.pitch, g.plane, valid, tbad, smax);
                     }
-                }
-                if (k == s0 - 2) {
-                    u0 = u;
-                    w0 = cons_to_prim(K, u);
-                } else if (k == s0 - 1) {
-                    u1 = u;
-                    w1 = cons_to_prim(K, u, ir1);
-                } else {
-                    T ir2;
-                    const Prim<T> w2 = cons_to_prim(K, u, ir2);
-                    Prim<T> wl1, wr1;
-                    trace(K, hdtdx, w0, w1, ir1, w2, wl1, wr1);  // cell k - 1
-                    Cons<T> fhi = flo;
-                    if (k >= s0 + 1) fhi = FluxOp<T, VAR>::eval(a, wr0, wl1, redo, nfb);  // k-2 | k-1
-                    if (k >= s0 + 2) {
-                        // conservative update of cell k - 2
-                        Cons<T> out;
-                        out.r = u0.r - dtdx * (fhi.r - flo.r);
-                        out.mn = u0.mn - dtdx * (fhi.mn - flo.mn);
-                        out.mt = u0.mt - dtdx * (fhi.mt - flo.mt);
-                        out.E = u0.E - dtdx * (fhi.E - flo.E);
-                        const int ko = k - 2;
-                        if (DIR == DIR_X) {
-                            const int co = (ko - kfirst) / C, jo = (ko - kfirst) % C;
-                            write_slot_x<T>(ring + (co % S) * SLOT, lane, jo, out);
-                        } else if (valid) {
-                            T* d = a.dst + g.off + (long long)ko * g.pitch + line;
-                            d[0] = out.r;
-                            d[PN * g.plane] = out.mn;
-                            d[PT * g.plane] = out.mt;
-                            d[3 * g.plane] = out.E;
-                        }
-                        if (valid) {
-                            tbad |= (out.r > T(0)) ? 0u : STATUS_BAD_RHO;
-                            tbad |= (out.E > T(0)) ? 0u : STATUS_BAD_E;
-                            if (a.which == 1) {
-                                // CFL wave speed of the new state (next step's dt)
-                                T ir;
-                                const Prim<T> w = cons_to_prim(K, out, ir);
-                                const T au = tabs(w.u), av = tabs(w.v);
-                                const T sp = ((au > av) ? au : av) + tsqrt(K.gamma * w.p * ir);
-                                smax = (sp <= smax) ? smax : sp;
-                            }
-                        }
-                    }
-                    flo = fhi;
-                    u0 = u1; u1 = u;
-                    w0 = w1; w1 = w2; ir1 = ir2;
-                    wr0 = wr1;
                 }
             }
             __syncwarp();
-
-            if (DIR == DIR_X) {
-                // chunk c-1 is complete: store it when it holds results
-                if (c >= 1) {
-                    const int ks = kfirst + (c - 1) * C;
-                    if (ks >= s0 && ks < s1) {
-                        fence_proxy_async_smem();
-                        __syncwarp();
-                        if (lane == 0) tma_store_3d(mdst, ks, line0, 0, ring + ((c - 1) % S) * SLOT);
-                    }
-                }
-                if (lane == 0) {
-                    bulk_commit();
-                    // refill the slot of chunk c-2 once its store has read it
-                    const int cr = c - 2 + S;
-                    if (c >= 2 && cr < nch) {
-                        bulk_wait_read<1>();
-                        fence_proxy_async_smem();
-                        issue(cr);
-                    }
-                }
-            } else {
-                if (lane == 0 && c + S < nch) {
-                    fence_proxy_async_smem();
-                    issue(c + S);
-                }
+            if (lane == 0 && c + S < nch) {
+                fence_proxy_async_smem();
+                ring.issue(sl, msrc, line0, kfirst + (c + S) * C);
             }
         }
         if (aborted) break;
-
-        if (DIR == DIR_X) {
-            // the last chunk when it holds results (ragged end of a line)
-            const int ks = kfirst + (nch - 1) * C;
-            if (ks >= s0 && ks < s1) {
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) tma_store_3d(mdst, ks, line0, 0, ring + ((nch - 1) % S) * SLOT);
-            }
-            if (lane == 0) {
-                bulk_commit();
-                bulk_wait_read<0>();  // every slot free before the next tile
-            }
-            __syncwarp();
-        }
-
-        // ---- tile epilogue: queue for the FP32 second pass, or publish ----
-        if (VAR == VAR_F32_MAIN && __any_sync(0xffffffffu, redo && valid)) {
-            if (lane == 0) {
-                const unsigned i = atomicAdd(&a.ctr->redo_count[a.which], 1u);
-                a.redo_list[a.which * a.redo_cap + i] = t;
-            }
-        } else {
-            kbad |= tbad;
-            if (a.which == 1) {
-                double m = (double)smax;
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double v = __shfl_xor_sync(0xffffffffu, m, o);
-                    m = (v <= m) ? m : v;
-                }
-                if (lane == 0)
-                    atomicMax(&a.run[tile.grid].wmax[acc], (unsigned long long)__double_as_longlong(m));
-            }
-        }
+        finish_tile<T, VAR, WHICH>(a, t, tile.grid, acc, redo && valid, tbad, smax, kbad, lane);
     }
 
-    if (aborted) {
-        // record the timeout and wait (bounded) for this warp's copies in flight
-        if (lane == 0) {
-            atomicOr(&a.ctr->status, STATUS_TIMEOUT);
-            for (int s = 0; s < S; ++s)
-                if (pending & (1u << s)) mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
-        }
+    if (aborted && lane == 0) {
+        atomicOr(&a.ctr->status, STATUS_TIMEOUT);
+        ring.drain();
     }
-    if (DIR == DIR_X && lane == 0) bulk_wait<0>();  // results globally visible
-
     for (int o = 16; o > 0; o >>= 1) {
         nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
         kbad |= __shfl_xor_sync(0xffffffffu, kbad, o);
@@ -488,28 +459,218 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR>::value))
     }
 }
 
+// =================================================================== x ===
+// Lines are rows; a warp task is one row span [x0, x1).  The span is read in
+// 64-cell segments (TMA box 64 cells x 1 row x 4 planes); lane l holds cells
+// A = x + 2l and A + 1 of segment x.  From its left neighbour (lane l-1, or
+// for lane 0 the last lane of the previous segment, kept in a carry) it takes
+// the primitives of A-2, A-1, the right face of A-2 and the flux at
+// (A-3)+1/2; it then traces cells A-1 and A, solves the interfaces
+// (A-2)+1/2 and (A-1)+1/2 and updates cells A-2 and A-1, one lane-width
+// behind the data, so every interface is solved once and a warp writes 64
+// consecutive cells per plane.  The old states of A-2, A-1 are read back from
+// the ring (lane 0: from the previous segment's slot).
+template <class T>
+__device__ __forceinline__ T from_left(T v, T& carry, int lane) {
+    const T t = __shfl_sync(0xffffffffu, v, (lane + 31) & 31);
+    const T r = (lane == 0) ? carry : t;
+    carry = t;  // lane 0 keeps the last lane's value for the next segment
+    return r;
+}
+template <class T>
+__device__ __forceinline__ Prim<T> from_left(const Prim<T>& v, Prim<T>& c, int lane) {
+    return Prim<T>{from_left(v.r, c.r, lane), from_left(v.u, c.u, lane), from_left(v.v, c.v, lane),
+                   from_left(v.p, c.p, lane)};
+}
+template <class T>
+__device__ __forceinline__ Cons<T> from_left(const Cons<T>& v, Cons<T>& c, int lane) {
+    return Cons<T>{from_left(v.r, c.r, lane), from_left(v.mn, c.mn, lane), from_left(v.mt, c.mt, lane),
+                   from_left(v.E, c.E, lane)};
+}
+
+// two consecutive cells (j, j+1) of every plane of a ring slot (x layout [q][64])
+template <class T>
+__device__ __forceinline__ void read_pair(const unsigned char* slot, int j, Cons<T>& c0, Cons<T>& c1) {
+    constexpr int PB = 64 * (int)sizeof(T);
+    T v[4][2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (sizeof(T) == 4) {
+            const float2 f = *reinterpret_cast<const float2*>(slot + q * PB + j * sizeof(T));
+            v[q][0] = (T)f.x; v[q][1] = (T)f.y;
+        } else {
+            const double2 f = *reinterpret_cast<const double2*>(slot + q * PB + j * sizeof(T));
+            v[q][0] = (T)f.x; v[q][1] = (T)f.y;
+        }
+    }
+    c0 = Cons<T>{v[0][0], v[1][0], v[2][0], v[3][0]};
+    c1 = Cons<T>{v[0][1], v[1][1], v[2][1], v[3][1]};
+}
+
+template <class T>
+__device__ __forceinline__ void store_pair(T* __restrict__ p, long long plane, const Cons<T>& a, const Cons<T>& b,
+                                           bool lo, bool hi) {
+    const T va[4] = {a.r, a.mn, a.mt, a.E}, vb[4] = {b.r, b.mn, b.mt, b.E};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        T* d = p + q * plane;
+        if (lo && hi) {
+            if (sizeof(T) == 4) *reinterpret_cast<float2*>(d) = make_float2((float)va[q], (float)vb[q]);
+            else *reinterpret_cast<double2*>(d) = make_double2((double)va[q], (double)vb[q]);
+        } else if (lo) {
+            d[0] = va[q];
+        }
+    }
+}
+
+template <class T, int VAR, int WHICH>
+__global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::value))
+    sweep_x_kernel(const SweepArgs<T> a) {
+    constexpr int SEG = kXSegment;
+    constexpr int S = ring_slots(DIR_X);
+    constexpr int SLOT = slot_bytes<T>(DIR_X);
+    constexpr int NWARPS = kSweepThreads / 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpRing<S, SLOT> ring;
+    ring.init(smem, warp, NWARPS, lane);
+
+    const Consts<T>& K = a.K;
+    const unsigned acc = a.ctr->acc;
+    unsigned kbad = 0, nfb = 0;
+    bool aborted = false;
+
+    for (;;) {
+        const int t = claim_tile<T, VAR>(a, lane);
+        if (t < 0) break;
+        const Tile tile = a.tiles[t];
+        const GridDesc g = a.grids[tile.grid];
+        const double dt = a.run[tile.grid].dt;
+        const int n = g.nx, row = tile.line0;
+        const int x0 = tile.cell0, x1 = tile.cell0 + tile.ncell;
+        const int nseg = (tile.ncell + 1) / SEG + 1;
+        const int bclo = g.bc[0], bchi = g.bc[1];
+        const CUtensorMap* msrc = a.maps + ((size_t)tile.grid * 2 + a.src_buf) * 2 + DIR_X;
+        if (lane == 0)
+            for (int c = 0; c < S && c < nseg; ++c) ring.issue(c, msrc, x0 + c * SEG, row);
+
+        const T dtdx = T(dt / g.h);
+        const T hdtdx = T(-0.5) * dtdx;
+        T* __restrict__ drow = a.dst + g.off + (long long)row * g.pitch;
+
+        // carries into lane 0 of the first segment: cells x0-2 and x0-1
+        Prim<T> cWA, cWB, cWR;
+        T cirB;
+        {
+            const Cons<T> um2 = (x0 >= 2) ? global_cell<T, DIR_X>(a.src, g, row, x0 - 2)
+                                          : ghost_cell<T, DIR_X>(a.src, g, row, x0 - 2, n, bclo, bchi);
+            const Cons<T> um1 = (x0 >= 1) ? global_cell<T, DIR_X>(a.src, g, row, x0 - 1)
+                                          : ghost_cell<T, DIR_X>(a.src, g, row, x0 - 1, n, bclo, bchi);
+            cWA = cons_to_prim(K, um2);
+            cWB = cons_to_prim(K, um1, cirB);
+            cWR = cWB;  // right face of x0-2: only feeds outputs before x0
+        }
+        Cons<T> cF = {T(0), T(0), T(0), T(0)};
+        T smax = T(0);
+        unsigned tbad = 0;
+        bool redo = false;
+
+        for (int sgi = 0; sgi < nseg; ++sgi) {
+            const int x = x0 + sgi * SEG;
+            const int sl = sgi % S;
+            if (!ring.wait(sl, lane)) { aborted = true; break; }
+            const unsigned char* cur = ring.slot(sl);
+            const int A = x + 2 * lane;
+            Cons<T> uA, uB;
+            read_pair<T>(cur, 2 * lane, uA, uB);
+            if (x + SEG > n) {
+                // positions n and n+1 are boundary cells; beyond them nothing is used
+                if (A == n || A == n + 1) uA = ghost_cell<T, DIR_X>(a.src, g, row, A, n, bclo, bchi);
+                if (A + 1 == n || A + 1 == n + 1) uB = ghost_cell<T, DIR_X>(a.src, g, row, A + 1, n, bclo, bchi);
+            }
+            T irA, irB;
+            const Prim<T> WA = cons_to_prim(K, uA, irA);
+            const Prim<T> WB = cons_to_prim(K, uB, irB);
+            const Prim<T> Wm2 = from_left(WA, cWA, lane);   // cell A-2
+            const Prim<T> Wm1 = from_left(WB, cWB, lane);   // cell A-1
+            const T irm1 = from_left(irB, cirB, lane);
+            Prim<T> WL1, WR1, WL2, WR2;
+            trace(K, hdtdx, Wm2, Wm1, irm1, WA, WL1, WR1);  // cell A-1
+            trace(K, hdtdx, Wm1, WA, irA, WB, WL2, WR2);    // cell A
+            const Prim<T> WRm = from_left(WR2, cWR, lane);  // right face of A-2
+            bool r1 = false, r2 = false;
+            const Cons<T> F1 = FluxOp<T, VAR>::eval(a, WRm, WL1, r1, nfb);  // (A-2)+1/2
+            const Cons<T> F2 = FluxOp<T, VAR>::eval(a, WR1, WL2, r2, nfb);  // (A-1)+1/2
+            const Cons<T> F0 = from_left(F2, cF, lane);     // (A-3)+1/2
+            // old states of A-2, A-1 (lane 0: the previous segment's last two)
+            Cons<T> o2, o1;
+            if (lane > 0) read_pair<T>(cur, 2 * lane - 2, o2, o1);
+            else read_pair<T>(ring.slot(sgi > 0 ? (sgi - 1) % S : sl), SEG - 2, o2, o1);
+            const Cons<T> n2 = update(o2, dtdx, F1, F0);
+            const Cons<T> n1 = update(o1, dtdx, F2, F1);
+            const bool lo = (A - 2 >= x0) && (A - 2 < x1);
+            const bool hi = (A - 1 >= x0) && (A - 1 < x1);
+            // a second-pass request counts only for interfaces feeding stored cells
+            redo |= (r1 && (lo || hi)) || (r2 && (hi || (A >= x0 && A < x1)));
+            if (lo) {
+                store_pair<T>(drow + (A - 2), g.plane, n2, n1, lo, hi);
+                check_cell<T, WHICH>(K, n2, tbad, smax);
+                if (hi) check_cell<T, WHICH>(K, n1, tbad, smax);
+            }
+            __syncwarp();
+            // the previous segment's slot is free now
+            if (lane == 0 && sgi >= 1 && sgi - 1 + S < nseg) {
+                fence_proxy_async_smem();
+                ring.issue((sgi - 1) % S, msrc, x0 + (sgi - 1 + S) * SEG, row);
+            }
+        }
+        if (aborted) break;
+        finish_tile<T, VAR, WHICH>(a, t, tile.grid, acc, redo, tbad, smax, kbad, lane);
+    }
+
+    if (aborted && lane == 0) {
+        atomicOr(&a.ctr->status, STATUS_TIMEOUT);
+        ring.drain();
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
+        kbad |= __shfl_xor_sync(0xffffffffu, kbad, o);
+    }
+    if (lane == 0) {
+        if (kbad) atomicOr(&a.ctr->status, kbad);
+        if (nfb) atomicAdd(&a.ctr->riemann_fp64, (unsigned long long)nfb);
+    }
+}
+
+// ---------------------------------------------------------------- launch --
+template <class T, int VAR, int WHICH, int DIR>
+struct KernelOf {
+    static constexpr auto fn() { return DIR == DIR_X ? sweep_x_kernel<T, VAR, WHICH> : sweep_y_kernel<T, VAR, WHICH>; }
+};
+
 // Launch (the dynamic shared-memory limit was raised by occupancy_one, which
 // the context calls for every variant it uses before the first launch).
 template <class T, int DIR, int VAR>
 cudaError_t launch_one(const SweepArgs<T>& a, int nctas, cudaStream_t s) {
     constexpr int smem = sweep_smem_bytes<T>(DIR);
-    sweep_kernel<T, DIR, VAR><<<nctas, kSweepThreads, smem, s>>>(a);
+    if (a.which == 0) KernelOf<T, VAR, 0, DIR>::fn()<<<nctas, kSweepThreads, smem, s>>>(a);
+    else KernelOf<T, VAR, 1, DIR>::fn()<<<nctas, kSweepThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-// Raise the kernel's dynamic shared-memory limit and return its resident
-// CTAs per SM.
+// Raise the kernels' dynamic shared-memory limit and return their resident
+// CTAs per SM (the smaller of the two sweep-order instances).
 template <class T, int DIR, int VAR>
 int occupancy_one() {
     constexpr int smem = sweep_smem_bytes<T>(DIR);
-    if (cudaFuncSetAttribute(sweep_kernel<T, DIR, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-        cudaSuccess)
-        return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, DIR, VAR>, kSweepThreads, smem) !=
-        cudaSuccess)
-        return 0;
-    return nb;
+    int best = 1 << 30;
+    for (auto fn : {KernelOf<T, VAR, 0, DIR>::fn(), KernelOf<T, VAR, 1, DIR>::fn()}) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kSweepThreads, smem) != cudaSuccess) return 0;
+        best = nb < best ? nb : best;
+    }
+    return best;
 }
 
 }  // namespace hydro

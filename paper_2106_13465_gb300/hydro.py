@@ -46,7 +46,7 @@ class hydro_params(ctypes.Structure):
 
 class hydro_tuning(ctypes.Structure):
     _fields_ = [("tile_len", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("graph_steps", ctypes.c_int)]
+                ("graph_steps", ctypes.c_int), ("span_len", ctypes.c_int)]
 
 
 class hydro_stats(ctypes.Structure):
@@ -250,8 +250,9 @@ class Context:
     def __exit__(self, *exc):
         self.close()
 
-    def set_tuning(self, tile_len: int = 0, ctas_per_sm: int = 0, graph_steps: int = 20) -> None:
-        self._check(hydro_set_tuning(self.ctx, hydro_tuning(tile_len, ctas_per_sm, graph_steps)))
+    def set_tuning(self, tile_len: int = 0, ctas_per_sm: int = 0, graph_steps: int = 20,
+                   span_len: int = 0) -> None:
+        self._check(hydro_set_tuning(self.ctx, hydro_tuning(tile_len, ctas_per_sm, graph_steps, span_len)))
 
     def set_state(self, grid: int, U) -> None:
         if hasattr(U, "data_ptr"):
