@@ -54,6 +54,9 @@ WORKLOADS = {
     "batch512_fp64": (lambda: pr.batch(512), 64, "512 ragged grids, sides in [32,512], FP64"),
     "kh16384_fp32": (lambda: [pr.kelvin_helmholtz(16384)], 32,
                      "16384x16384 periodic Kelvin-Helmholtz, FP32"),
+    "explosion10000_fp64": (lambda: [pr.sedov(10000)], 64,
+                            "10000x10000 point explosion (Sedov blast in the corner), FP64: the "
+                            "grid of the paper's own runs (10 steps there)"),
 }
 DEFAULT_WORKLOAD = "sedov2048_fp64"
 
@@ -231,9 +234,16 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     esz = 8 if prec == 64 else 4
     state_bytes = sum(4 * p.ny * ((p.nx + 31) // 32 * 32) * esz for p in pbs)
 
+    tuning = None
+    if args.autotune:
+        from paper_2106_13465_gb300.autotune import autotune
+        tuning = autotune(pbs, precision=prec, steps=3, warmup=1).tuning()
+
     stream = torch.cuda.Stream()
     ctx = H.Context([(p.nx, p.ny, p.h, p.bc) for p in pbs], precision=prec,
                     stream=stream.cuda_stream)
+    if tuning:
+        ctx.set_tuning(graph_steps=20, **tuning)
     for g, p in enumerate(pbs):
         ctx.set_state(g, p.U)
     ctx.step(args.warmup)
@@ -297,6 +307,27 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     stats = ctx.stats()
     ctx.close()
 
+    # ---- FP32 against FP64 on the same dt sequence (outside the timing) ----
+    precision_report = None
+    if prec == 32 and args.l1_steps > 0 and world == 1:
+        grids = [(p.nx, p.ny, p.h, p.bc) for p in pbs]
+        with H.Context(grids, precision=64) as c64:
+            for g, p in enumerate(pbs):
+                c64.set_state(g, p.U)
+            dts = c64.step(args.l1_steps, record_dt=True)
+            ref = [c64.get_state(g)[0] for g in range(len(pbs))]
+        with H.Context(grids, precision=32) as c32:
+            for g, p in enumerate(pbs):
+                c32.set_state(g, p.U)
+            c32.step(args.l1_steps, dt_override=dts)
+            got = [c32.get_state(g)[0] for g in range(len(pbs))]
+            fb = c32.stats()["riemann_fp64"]
+        num = sum(float(np.abs(a - b).sum()) for a, b in zip(got, ref))
+        den = sum(float(np.abs(b).sum()) for b in ref)
+        precision_report = {"l1_rho_rel_fp32_vs_fp64": num / den, "steps": args.l1_steps,
+                            "dt": "FP64 run's dt sequence replayed in FP32",
+                            "riemann_fp64_solves": fb}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -338,7 +369,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "data": "synthetic",
         "config": {"workload": wl, "description": desc, "grids": len(pbs), "cells": cells,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": f"state {2 * state_bytes / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush"},
+                   "l2": f"state {2 * state_bytes / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush",
+                   "tuning": tuning or "model default"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -346,6 +378,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "clocks": clocks,
         "kernels_ms": {"prologue": prologue_ms, "sweep": sweep_ms},
         "riemann_fp64_fallbacks": stats["riemann_fp64"],
+        "precision_report": precision_report,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -361,6 +394,10 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--l1-steps", type=int, default=0,
+                    help="FP32 workloads: also report the L1 density error against FP64 after this many steps")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time candidate launch shapes first and use the fastest")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

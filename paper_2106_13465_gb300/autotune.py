@@ -1,0 +1,107 @@
+"""Autotuner of the sweep launch shape.
+
+For a given set of grids and precision it times candidate launch shapes
+(`hydro_tuning`: rows per y-sweep tile, cells per x-sweep warp task, CTAs per
+SM) through the C ABI and keeps the fastest.  Every candidate must reproduce
+the reference run's final states bit for bit: a cell's update depends only
+on its stencil (Figs. 1-2), so the launch shape may change the speed but
+never the result, and a candidate that changed it would be a bug -- it is
+rejected and reported.
+
+The search is coordinate descent from the library's model-based defaults:
+the y tile length first, then the x span length, then CTAs per SM, each
+candidate timed over `steps` steps (hydro_step_profiled: CUDA events around
+each sweep launch) after restoring the same initial states.
+"""
+from __future__ import annotations
+
+import json
+import os
+from dataclasses import asdict, dataclass, field
+
+import numpy as np
+
+from . import hydro as H
+
+Y_TILES = (0, 16, 24, 32, 48, 64, 96, 128)
+X_SPANS = (0, 128, 256, 512, 1024, 2048)
+CTAS = (0, 1, 2, 3, 4, 6)
+
+
+@dataclass
+class TuneResult:
+    tile_len: int = 0
+    span_len: int = 0
+    ctas_per_sm: int = 0
+    sweep_ms: float = float("inf")
+    trials: list = field(default_factory=list)
+    rejected: list = field(default_factory=list)
+
+    def tuning(self) -> dict:
+        return {"tile_len": self.tile_len, "span_len": self.span_len, "ctas_per_sm": self.ctas_per_sm}
+
+
+def coordinate_descent(evaluate, axes):
+    """Minimise evaluate(config) over a dict of axes {name: candidates}, one
+    axis at a time starting from the first candidate of each; evaluate returns
+    a time or None (candidate rejected).  Returns (best_config, best_time,
+    trials)."""
+    cfg = {k: v[0] for k, v in axes.items()}
+    best = evaluate(dict(cfg))
+    trials = [(dict(cfg), best)]
+    if best is None:
+        raise RuntimeError("the default configuration was rejected")
+    for name, cands in axes.items():
+        for v in cands[1:]:
+            trial = dict(cfg, **{name: v})
+            t = evaluate(trial)
+            trials.append((trial, t))
+            if t is not None and t < best:
+                best, cfg = t, trial
+    return cfg, best, trials
+
+
+def autotune(problems, precision: int = H.PREC_FP64, steps: int = 4, warmup: int = 1,
+             y_tiles=Y_TILES, x_spans=X_SPANS, ctas=CTAS) -> TuneResult:
+    """problems: objects with .U ([4, ny, nx] FP64), .h and .bc."""
+    grids = [(p.U.shape[2], p.U.shape[1], p.h, p.bc) for p in problems]
+    res = TuneResult()
+    ref = {}
+    with H.Context(grids, precision=precision) as ctx:
+        def run(cfg):
+            try:
+                ctx.set_tuning(tile_len=cfg["tile_len"], span_len=cfg["span_len"],
+                               ctas_per_sm=cfg["ctas_per_sm"], graph_steps=20)
+            except H.HydroError:
+                return None
+            for g, p in enumerate(problems):
+                ctx.set_state(g, p.U)
+            if warmup:
+                ctx.step_profiled(warmup)
+            ms = ctx.step_profiled(steps)
+            out = [ctx.get_state(g) for g in range(len(problems))]
+            if not ref:
+                ref["out"] = out
+            elif not all(np.array_equal(a, b) for a, b in zip(out, ref["out"])):
+                res.rejected.append(dict(cfg))
+                return None
+            return float(ms[:, 1:].sum() / steps)
+
+        axes = {"tile_len": list(y_tiles), "span_len": list(x_spans), "ctas_per_sm": list(ctas)}
+        cfg, best, trials = coordinate_descent(run, axes)
+    res.tile_len, res.span_len, res.ctas_per_sm = cfg["tile_len"], cfg["span_len"], cfg["ctas_per_sm"]
+    res.sweep_ms = best
+    res.trials = [{"tuning": c, "sweep_ms": t} for c, t in trials]
+    return res
+
+
+def save(res: TuneResult, path: str) -> None:
+    with open(path, "w") as f:
+        json.dump(asdict(res), f, indent=1)
+
+
+def load(path: str) -> TuneResult | None:
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return TuneResult(**json.load(f))

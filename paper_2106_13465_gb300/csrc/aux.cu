@@ -57,10 +57,7 @@ __global__ void cfl_reduce_kernel(const T* __restrict__ state, GridDesc g, int g
         const int j = (int)(c / g.nx), i = (int)(c - (long long)j * g.nx);
         const T* p = state + g.off + (long long)j * g.pitch + i;
         const Cons<T> u = {p[0], p[g.plane], p[2 * g.plane], p[3 * g.plane]};
-        T ir;
-        const Prim<T> w = cons_to_prim(K, u, ir);
-        const T au = tabs(w.u), av = tabs(w.v);
-        const T s = ((au > av) ? au : av) + tsqrt(K.gamma * w.p * ir);
+        const T s = cfl_speed(K, u);
         smax = (s <= smax) ? smax : s;
     }
     double m = (double)smax;

@@ -34,6 +34,8 @@ struct Consts {
     T G7;         // (g - 1) / 2
     T inv_g;      // 1 / g
     T hgp1;       // (g + 1) / 2
+    T sqg;        // sqrt(g)
+    T isqg;       // 1 / sqrt(g)
     T rho_floor;  // density floor
     T cf2g;       // c_floor^2 / g: p >= rho * cf2g
     T pmin;       // smallest pressure of the Riemann iteration, rho_floor * cf2g
@@ -48,7 +50,9 @@ template <class T> struct Cons { T r, mn, mt, E; };   // (rho, m_n, m_t, E)
 // IEEE double operations for T = double.  For T = float the translation
 // unit is built with fast single-precision division, square root and
 // power (approximate hardware instructions); see the build script.
-__device__ __forceinline__ double tpow(double x, double e) { return pow(x, e); }
+// FP64 powers through exp2(e log2 x): within a few ulp, and cheaper on the
+// FP64 pipe than the extra-precise pow
+__device__ __forceinline__ double tpow(double x, double e) { return exp2(e * log2(x)); }
 __device__ __forceinline__ float tpow(float x, float e) { return __powf(x, e); }
 __device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
@@ -87,15 +91,44 @@ __device__ __forceinline__ Prim<T> cons_to_prim(const Consts<T>& K, const Cons<T
     return cons_to_prim(K, U, ir);
 }
 
+// CFL wave speed of a cell, max(|u|, |v|) + c with c = sqrt(g p / rho);
+// in FP64 through one reciprocal square root, c = sqrt(g) p / sqrt(rho p).
+template <class T>
+__device__ __forceinline__ T cfl_speed(const Consts<T>& K, const Cons<T>& U) {
+    T ir;
+    const Prim<T> w = cons_to_prim(K, U, ir);
+    const T au = tabs(w.u), av = tabs(w.v);
+    T c;
+    if (sizeof(T) == 8) c = K.sqg * w.p * trsqrt(w.r * w.p);
+    else c = tsqrt(K.gamma * w.p * ir);
+    return ((au > av) ? au : av) + c;
+}
+
 // ---------------------------------------------------- slopes and trace --
 // minmod(a, b): 0 unless a and b are both > 0 or both < 0, then the one of
-// smaller magnitude.
-template <class T>
-__device__ __forceinline__ T minmod(T a, T b) {
-    T r = T(0);
-    if (a > T(0) && b > T(0)) r = (a < b) ? a : b;
-    if (a < T(0) && b < T(0)) r = (a > b) ? a : b;
-    return r;
+// smaller magnitude.  The sign tests run on the bit patterns (integer
+// pipe); the result is exactly a or b (or +0) as in the comparison form.
+__device__ __forceinline__ double minmod(double a, double b) {
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const bool take = ((ia ^ ib) >= 0) && ((ia << 1) != 0) && ((ib << 1) != 0);
+    const long long m = __double_as_longlong(fmin(fabs(a), fabs(b))) | (ia & (long long)0x8000000000000000ull);
+    return take ? __longlong_as_double(m) : 0.0;
+}
+__device__ __forceinline__ float minmod(float a, float b) {
+    const int ia = __float_as_int(a), ib = __float_as_int(b);
+    const bool take = ((ia ^ ib) >= 0) && ((ia << 1) != 0) && ((ib << 1) != 0);
+    const int m = __float_as_int(fminf(fabsf(a), fabsf(b))) | (ia & (int)0x80000000u);
+    return take ? __int_as_float(m) : 0.0f;
+}
+
+// x > 0 for x not NaN (positive finite or +inf), tested on the bit pattern.
+__device__ __forceinline__ bool positive(double x) {
+    const long long i = __double_as_longlong(x);
+    return i > 0 && i <= 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool positive(float x) {
+    const int i = __float_as_int(x);
+    return i > 0 && i <= 0x7f800000;
 }
 
 // MUSCL-Hancock trace of the cell with primitive state W0 between Wm and Wp
@@ -158,17 +191,20 @@ template <class T>
 __device__ __forceinline__ Side<T> make_side(const Consts<T>& K, const Prim<T>& W) {
     Side<T> s;
     s.r = W.r; s.u = W.u; s.v = W.v; s.p = W.p;
-    T ir;
     if (sizeof(T) == 8) {
-        const T irp = T(1) / (W.r * W.p);  // one division for 1/rho and 1/p
-        ir = W.p * irp;
-        s.ip = W.r * irp;
+        // y = 1/sqrt(rho p) gives c = sqrt(g) p y, 1/p = rho y^2 and
+        // 1/(rho c) = y / sqrt(g): one reciprocal square root per side
+        const T y = trsqrt(W.r * W.p);
+        s.c = K.sqg * W.p * y;
+        s.ip = W.r * y * y;
+        s.irc = K.isqg * y;
     } else {
-        ir = T(1) / W.r;
+        // FP32: rho p can underflow at the floors, so two reciprocals
+        const T ir = T(1) / W.r;
         s.ip = T(1) / W.p;
+        s.c = tsqrt(K.gamma * W.p * ir);
+        s.irc = s.c * s.ip * K.inv_g;
     }
-    s.c = tsqrt(K.gamma * W.p * ir);
-    s.irc = s.c * s.ip * K.inv_g;
     s.iA = K.hgp1 * W.r;
     s.B = K.G6 * W.p;
     s.cG4 = s.c * K.G4;
@@ -225,16 +261,19 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
         pressure_fn(K, L, p, fl, al, bl, pzl);
         pressure_fn(K, R, p, fr, ar, br, pzr);
         const T F = fl + fr + du;
-        const T g = F / tfma(p, bl + br, al + ar);     // Newton step / p
+        // Newton step / p (F == 0: p is the root, the step is exactly 0)
+        const T g = (F == T(0)) ? T(0) : F / tfma(p, bl + br, al + ar);
         T d = g * p;                                    // the step p - p_new
         T pn = p - d;
         T rel = g;                                      // d / p
         if (pn < K.pmin) { pn = K.pmin; floored = true; d = p - pn; rel = d / p; }
         if (tabs(d) <= K.tol * pn) {
-            fl -= tfma(al, rel, bl * d);
-            fr -= tfma(ar, rel, br * d);
-            if (pzl > T(0)) pzl = tfma(-K.z * pzl, rel, pzl);
-            if (pzr > T(0)) pzr = tfma(-K.z * pzr, rel, pzr);
+            if (d != T(0)) {
+                fl -= tfma(al, rel, bl * d);
+                fr -= tfma(ar, rel, br * d);
+                if (pzl > T(0)) pzl = tfma(-K.z * pzl, rel, pzl);
+                if (pzr > T(0)) pzr = tfma(-K.z * pzr, rel, pzr);
+            }
             p = pn;
             conv = true;
             break;

@@ -45,6 +45,8 @@ Consts<T> make_consts(const hydro_params& p, double tol) {
     K.G7 = (T)((g - 1.0) / 2.0);
     K.inv_g = (T)(1.0 / g);
     K.hgp1 = (T)((g + 1.0) / 2.0);
+    K.sqg = (T)std::sqrt(g);
+    K.isqg = (T)(1.0 / std::sqrt(g));
     K.rho_floor = (T)p.rho_floor;
     K.cf2g = (T)(p.c_floor * p.c_floor / g);
     K.pmin = (T)(p.rho_floor * (p.c_floor * p.c_floor / g));

@@ -273,13 +273,10 @@ __device__ __forceinline__ void finish_tile(const SweepArgs<T>& a, int t, int gr
 // Status bits and (second sweep) CFL wave speed of one new cell state.
 template <class T, int WHICH>
 __device__ __forceinline__ void check_cell(const Consts<T>& K, const Cons<T>& out, unsigned& tbad, T& smax) {
-    tbad |= (out.r > T(0)) ? 0u : STATUS_BAD_RHO;
-    tbad |= (out.E > T(0)) ? 0u : STATUS_BAD_E;
+    tbad |= positive(out.r) ? 0u : STATUS_BAD_RHO;
+    tbad |= positive(out.E) ? 0u : STATUS_BAD_E;
     if (WHICH == 1) {
-        T ir;
-        const Prim<T> w = cons_to_prim(K, out, ir);
-        const T au = tabs(w.u), av = tabs(w.v);
-        const T sp = ((au > av) ? au : av) + tsqrt(K.gamma * w.p * ir);
+        const T sp = cfl_speed(K, out);
         smax = (sp <= smax) ? smax : sp;
     }
 }
