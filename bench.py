@@ -48,6 +48,8 @@ WORKLOADS = {
                        "4096x4096 periodic random-mode field, FP32 (profiling size)"),
     "modes8192_fp32": (lambda: [pr.random_modes(8192)], 32,
                        "8192x8192 periodic random-mode field, FP32"),
+    "modes2048_fp64": (lambda: [pr.random_modes(2048)], 64,
+                       "2048x2048 periodic random-mode field, FP64 (profiling size)"),
     "modes8192_fp64": (lambda: [pr.random_modes(8192)], 64,
                        "8192x8192 periodic random-mode field, FP64"),
     "batch512_fp32": (lambda: pr.batch(512), 32, "512 ragged grids, sides in [32,512], FP32"),
@@ -273,9 +275,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # ---- per-kernel durations (same stream, CUDA events per launch) -------
     kp = max(2, min(args.steps, 20))
+    kstep0 = ctx.get_step()
     kern = ctx.step_profiled(kp)
     sweep_ms = float(np.mean(kern[:, 1:]))
     prologue_ms = float(np.mean(kern[:, 0]))
+    # even steps sweep x first, odd steps y first
+    par = (kstep0 + np.arange(kp)) % 2
+    x_ms = float(np.mean(np.where(par == 0, kern[:, 1], kern[:, 2])))
+    y_ms = float(np.mean(np.where(par == 0, kern[:, 2], kern[:, 1])))
 
     # ---- end to end through the C ABI with host buffers -------------------
     ke = max(1, min(args.steps, 10))
@@ -376,7 +383,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "e2e": e2e,
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
-        "kernels_ms": {"prologue": prologue_ms, "sweep": sweep_ms},
+        "kernels_ms": {"prologue": prologue_ms, "sweep": sweep_ms, "x_sweep": x_ms, "y_sweep": y_ms},
         "riemann_fp64_fallbacks": stats["riemann_fp64"],
         "precision_report": precision_report,
     }

@@ -90,7 +90,9 @@ typedef struct {
  *   ctas_per_sm   resident CTAs per SM of the persistent sweep launches
  *                 (at most the occupancy limit)
  *   graph_steps   steps captured per CUDA graph (even, 0 = no graph)
- *   span_len      x sweep: cells of a row per warp task (a multiple of 64)
+ *   span_len      x sweep: results of a row per warp task (a multiple of 60:
+ *                 a warp walks a row in overlapping 64-cell segments that
+ *                 yield 60 results each)
  * tile_len and span_len default to the best makespan of a list-scheduling
  * model of the tile queue on the resident warps.  Results are bit-identical
  * for every admissible setting. */

@@ -24,7 +24,7 @@ import numpy as np
 from . import hydro as H
 
 Y_TILES = (0, 16, 24, 32, 48, 64, 96, 128)
-X_SPANS = (0, 128, 256, 512, 1024, 2048)
+X_SPANS = (0, 120, 240, 480, 960, 1920)
 CTAS = (0, 1, 2, 3, 4, 6)
 
 

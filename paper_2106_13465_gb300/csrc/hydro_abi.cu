@@ -156,9 +156,12 @@ hydro_status validate_params(const hydro_params* p) {
     return HYDRO_OK;
 }
 
+// x segments of a row of n cells: segment k covers results [60k-2, 60k+58).
+int x_segments(int n) { return (n + 2 + kXStride - 1) / kXStride; }
+
 // Tile work-lists.  y sweep: for each grid, columns in groups of 32 (one per
-// lane), rows in segments of len.  x sweep: for each grid and row, spans of
-// len cells (one warp task each).
+// lane), rows in runs of len.  x sweep: for each grid and row, runs of len
+// consecutive segments (one warp task each).
 void build_tiles(const std::vector<GridDesc>& gd, int dir, int len, std::vector<Tile>& out) {
     out.clear();
     for (int g = 0; g < (int)gd.size(); ++g) {
@@ -167,19 +170,19 @@ void build_tiles(const std::vector<GridDesc>& gd, int dir, int len, std::vector<
                 for (int c0 = 0; c0 < gd[g].ny; c0 += len)
                     out.push_back(Tile{g, l0, c0, std::min(len, gd[g].ny - c0)});
         } else {
+            const int ns = x_segments(gd[g].nx);
             for (int j = 0; j < gd[g].ny; ++j)
-                for (int c0 = 0; c0 < gd[g].nx; c0 += len)
-                    out.push_back(Tile{g, j, c0, std::min(len, gd[g].nx - c0)});
+                for (int k0 = 0; k0 < ns; k0 += len)
+                    out.push_back(Tile{g, j, k0, std::min(len, ns - k0)});
         }
     }
 }
 
 // Cost of a tile in cell units for the scheduling model: y, its cells plus
-// its 4-cell halo; x, the 64-cell segments its warp walks (one more than its
-// length needs) plus a fixed start-up.
+// its 4-cell halo; x, the 64 cells of each of its segments plus a start-up.
 double tile_cost(const Tile& t, int dir) {
     if (dir == DIR_Y) return t.ncell + 4.0;
-    return ((t.ncell + 1) / kXSegment + 1) * (double)kXSegment + 16.0;
+    return t.ncell * (double)kXSegment + 16.0;
 }
 
 // Makespan of the dynamic tile queue on `warps` resident warps (list
@@ -203,7 +206,7 @@ int auto_tile_len(const std::vector<GridDesc>& gd, int dir, int warps) {
         for (int L = 16; L <= 128; L += 4) cand.push_back(L);
         for (int L : {160, 192, 256, 384, 512}) cand.push_back(L);
     } else {
-        for (int L : {64, 128, 192, 256, 320, 384, 512, 640, 768, 1024, 1536, 2048, 4096}) cand.push_back(L);
+        for (int L : {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 48, 64, 128}) cand.push_back(L);
     }
     int best = cand[0];
     double best_span = 1e300;
@@ -262,7 +265,7 @@ hydro_status upload_tiles(hydro_ctx* c) {
         if (per_sm <= 0 || per_sm > occ) per_sm = occ;
         const int warps_per_cta = kSweepThreads / 32;
         const int resident_warps = c->nsm * per_sm * warps_per_cta;
-        const int chosen = d == DIR_X ? c->tuning.span_len : c->tuning.tile_len;
+        const int chosen = d == DIR_X ? c->tuning.span_len / kXStride : c->tuning.tile_len;
         const int L = chosen > 0 ? chosen : auto_tile_len(c->gd, d, resident_warps);
         c->tile_len_used[d] = L;
         std::vector<Tile> t;
@@ -521,8 +524,8 @@ hydro_status hydro_set_tuning(hydro_ctx* c, const hydro_tuning* t) {
     hydro_tuning n = *t;
     if (n.tile_len != 0 && (n.tile_len < 4 || n.tile_len > (1 << 24) || (n.tile_len & 3)))
         return fail(c, HYDRO_EINVAL, "tile_len must be 0 (automatic) or a multiple of 4 in [4, 2^24]");
-    if (n.span_len != 0 && (n.span_len < kXSegment || n.span_len > (1 << 24) || (n.span_len % kXSegment)))
-        return fail(c, HYDRO_EINVAL, "span_len must be 0 (automatic) or a multiple of 64 in [64, 2^24]");
+    if (n.span_len != 0 && (n.span_len < kXStride || n.span_len > (1 << 24) || (n.span_len % kXStride)))
+        return fail(c, HYDRO_EINVAL, "span_len must be 0 (automatic) or a multiple of 60 in [60, 2^24]");
     if (n.ctas_per_sm < 0 || n.ctas_per_sm > 64) return fail(c, HYDRO_EINVAL, "ctas_per_sm must be in [0, 64]");
     if (n.graph_steps < 0 || (n.graph_steps & 1) || n.graph_steps > 1000)
         return fail(c, HYDRO_EINVAL, "graph_steps must be even and in [0, 1000]");

@@ -14,13 +14,14 @@
 // Each grid and buffer also has two TMA tensor maps over this layout, a 3D
 // tensor (x, y, q) of extents (nx, ny, 4) with byte strides
 // (pitch * esz, plane * esz):
-//   x-sweep map: box (64 cells, 1 row, 4 planes)    -- one row segment
+//   x-sweep map: box (64 cells, 1 row, 4 planes)    -- one row segment,
+//                starting at x = -4 + 60 k
 //   y-sweep map: box (32 columns, 4 rows, 4 planes) -- 32 columns x 4 cells
 // stored at maps[(grid * 2 + buffer) * 2 + dir].
 //
 // Work lists.  y sweep: a tile is 32 columns (one per lane) x ncell rows.
-// x sweep: a tile is one row x ncell cells (a warp walks it in 64-cell
-// segments), stored as (grid, line0 = row, cell0 = first x, ncell).
+// x sweep: a tile is a run of consecutive segments of one row, stored as
+// (grid, line0 = row, cell0 = first segment index, ncell = segments).
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -43,7 +44,8 @@ constexpr int kSweepThreads = 128;  // threads per CTA of the sweep kernels
 
 // TMA ring geometry per warp.  x sweep: one slot holds a 64-cell segment of
 // one row, 4 planes; y sweep: one slot holds 4 rows x 32 columns, 4 planes.
-constexpr int kXSegment = 64;
+constexpr int kXSegment = 64;  // cells per x segment (2 per lane)
+constexpr int kXStride = 60;   // segments overlap by 4 cells; 60 results each
 __host__ __device__ constexpr int ring_slots(int dir) { return 4; }
 template <class T>
 __host__ __device__ constexpr int slot_bytes(int dir) {

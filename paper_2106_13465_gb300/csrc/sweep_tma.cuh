@@ -294,9 +294,9 @@ __device__ __forceinline__ Cons<T> update(const Cons<T>& u, T dtdx, const Cons<T
 template <class T, int VAR, int DIR>
 struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_Y> { static constexpr int value = 4; };
-template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_X> { static constexpr int value = 4; };
-template <> struct MinBlocks<double, VAR_F64, DIR_Y> { static constexpr int value = 2; };
-template <> struct MinBlocks<double, VAR_F64, DIR_X> { static constexpr int value = 2; };
+template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_X> { static constexpr int value = 6; };
+template <> struct MinBlocks<double, VAR_F64, DIR_Y> { static constexpr int value = 3; };
+template <> struct MinBlocks<double, VAR_F64, DIR_X> { static constexpr int value = 3; };
 
 // =================================================================== y ===
 // Lines are columns: lane l walks column line0 + l down a tile of rows
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
         const T dtdx = T(dt / g.h);
         const T hdtdx = T(-0.5) * dtdx;
         T* __restrict__ dcol = a.dst + g.off + line;
-        YWalk<T> w;
+        YWalk<T> w = {};
         T smax = T(0);
         unsigned tbad = 0;
         bool redo = false;
@@ -384,12 +384,56 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
             const int sl = c % S;
             if (!ring.wait(sl, lane)) { aborted = true; break; }
             const T* sp = reinterpret_cast<const T*>(ring.slot(sl));
+            const int kc = kfirst + c * C;
+            if (sizeof(T) == 8) {
+                // FP64: one copy of the per-cell arithmetic (the FP64 pipe,
+                // not issue, bounds this kernel; a small loop body keeps the
+                // instruction cache warm), warm-up and edges as uniform branches
+#pragma unroll 1
+                for (int j = 0; j < C; ++j) {
+                    const int k = kc + j;
+                    if (k > klast) break;
+                    Cons<T> u = Cons<T>{sp[(0 * C + j) * 32 + lane], sp[(2 * C + j) * 32 + lane],
+                                        sp[(1 * C + j) * 32 + lane], sp[(3 * C + j) * 32 + lane]};
+                    if (k < 0 || k >= n) u = ghost_cell<T, DIR_Y>(a.src, g, lsafe, k, n, bclo, bchi);
+                    if (k == s0 - 2) {
+                        w.u0 = u;
+                        w.w0 = cons_to_prim(K, u);
+                        continue;
+                    }
+                    T ir2;
+                    const Prim<T> w2 = cons_to_prim(K, u, ir2);
+                    if (k > s0 - 1) {
+                        Prim<T> wl1, wr1;
+                        trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
+                        Cons<T> fhi = w.flo;
+                        if (k > s0) fhi = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb);
+                        if (k > s0 + 1) {
+                            const Cons<T> out = update(w.u0, dtdx, fhi, w.flo);
+                            if (valid) {
+                                T* d = dcol + (long long)(k - 2) * g.pitch;
+                                d[0] = out.r;
+                                d[2 * g.plane] = out.mn;
+                                d[1 * g.plane] = out.mt;
+                                d[3 * g.plane] = out.E;
+                                check_cell<T, WHICH>(K, out, tbad, smax);
+                            }
+                        }
+                        w.flo = fhi;
+                        w.u0 = w.u1;
+                        w.w0 = w.w1;
+                        w.wr0 = wr1;
+                    }
+                    w.u1 = u;
+                    w.w1 = w2;
+                    w.ir1 = ir2;
+                }
+            } else {
             Cons<T> cell[C];
 #pragma unroll
             for (int j = 0; j < C; ++j)
                 cell[j] = Cons<T>{sp[(0 * C + j) * 32 + lane], sp[(2 * C + j) * 32 + lane],
                                   sp[(1 * C + j) * 32 + lane], sp[(3 * C + j) * 32 + lane]};
-            const int kc = kfirst + c * C;
             if (c > 0 && kc + C - 1 < n && kc + C - 1 <= klast) {
                 // steady state: four interior positions, each completes a row
 #pragma unroll
@@ -432,6 +476,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                     }
                 }
             }
+            }
             __syncwarp();
             if (lane == 0 && c + S < nch) {
                 fence_proxy_async_smem();
@@ -457,38 +502,37 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
 }
 
 // =================================================================== x ===
-// Lines are rows; a warp task is one row span [x0, x1).  The span is read in
-// 64-cell segments (TMA box 64 cells x 1 row x 4 planes); lane l holds cells
-// A = x + 2l and A + 1 of segment x.  From its left neighbour (lane l-1, or
-// for lane 0 the last lane of the previous segment, kept in a carry) it takes
-// the primitives of A-2, A-1, the right face of A-2 and the flux at
-// (A-3)+1/2; it then traces cells A-1 and A, solves the interfaces
-// (A-2)+1/2 and (A-1)+1/2 and updates cells A-2 and A-1, one lane-width
-// behind the data, so every interface is solved once and a warp writes 64
-// consecutive cells per plane.  The old states of A-2, A-1 are read back from
-// the ring (lane 0: from the previous segment's slot).
+// Lines are rows.  A row is covered by overlapping 64-cell segments that
+// start at x = -4 + 60 k (TMA box 64 cells x 1 row x 4 planes; the start is
+// 16-byte aligned for FP32 and FP64) and each produce the 60 cells
+// [60 k - 2, 60 k + 58).  Lane l holds cells A = x + 2l and B = A + 1.  From
+// lane l-1 it takes the primitives of A-1 and the right face of A-1, from
+// lane l+1 the primitives of B+1 and the flux at B+1/2; it traces A and B,
+// solves the interfaces A-1/2 and A+1/2 and updates A and B.  Lanes 1..30
+// hold the 60 results (lanes 0 and 31 only feed their neighbours), so a
+// segment needs nothing from the previous one and a warp writes 60
+// consecutive cells per plane.  A warp task is a run of consecutive segments
+// of one row: (grid, line0 = row, cell0 = first segment, ncell = segments).
 template <class T>
-__device__ __forceinline__ T from_left(T v, T& carry, int lane) {
-    const T t = __shfl_sync(0xffffffffu, v, (lane + 31) & 31);
-    const T r = (lane == 0) ? carry : t;
-    carry = t;  // lane 0 keeps the last lane's value for the next segment
-    return r;
+__device__ __forceinline__ Prim<T> shfl_up1(const Prim<T>& v) {
+    return Prim<T>{__shfl_up_sync(0xffffffffu, v.r, 1), __shfl_up_sync(0xffffffffu, v.u, 1),
+                   __shfl_up_sync(0xffffffffu, v.v, 1), __shfl_up_sync(0xffffffffu, v.p, 1)};
 }
 template <class T>
-__device__ __forceinline__ Prim<T> from_left(const Prim<T>& v, Prim<T>& c, int lane) {
-    return Prim<T>{from_left(v.r, c.r, lane), from_left(v.u, c.u, lane), from_left(v.v, c.v, lane),
-                   from_left(v.p, c.p, lane)};
+__device__ __forceinline__ Prim<T> shfl_down1(const Prim<T>& v) {
+    return Prim<T>{__shfl_down_sync(0xffffffffu, v.r, 1), __shfl_down_sync(0xffffffffu, v.u, 1),
+                   __shfl_down_sync(0xffffffffu, v.v, 1), __shfl_down_sync(0xffffffffu, v.p, 1)};
 }
 template <class T>
-__device__ __forceinline__ Cons<T> from_left(const Cons<T>& v, Cons<T>& c, int lane) {
-    return Cons<T>{from_left(v.r, c.r, lane), from_left(v.mn, c.mn, lane), from_left(v.mt, c.mt, lane),
-                   from_left(v.E, c.E, lane)};
+__device__ __forceinline__ Cons<T> shfl_down1(const Cons<T>& v) {
+    return Cons<T>{__shfl_down_sync(0xffffffffu, v.r, 1), __shfl_down_sync(0xffffffffu, v.mn, 1),
+                   __shfl_down_sync(0xffffffffu, v.mt, 1), __shfl_down_sync(0xffffffffu, v.E, 1)};
 }
 
 // two consecutive cells (j, j+1) of every plane of a ring slot (x layout [q][64])
 template <class T>
 __device__ __forceinline__ void read_pair(const unsigned char* slot, int j, Cons<T>& c0, Cons<T>& c1) {
-    constexpr int PB = 64 * (int)sizeof(T);
+    constexpr int PB = kXSegment * (int)sizeof(T);
     T v[4][2];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -523,7 +567,7 @@ __device__ __forceinline__ void store_pair(T* __restrict__ p, long long plane, c
 template <class T, int VAR, int WHICH>
 __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::value))
     sweep_x_kernel(const SweepArgs<T> a) {
-    constexpr int SEG = kXSegment;
+    constexpr int SEG = kXSegment, STEP = kXStride;
     constexpr int S = ring_slots(DIR_X);
     constexpr int SLOT = slot_bytes<T>(DIR_X);
     constexpr int NWARPS = kSweepThreads / 32;
@@ -536,6 +580,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
     const unsigned acc = a.ctr->acc;
     unsigned kbad = 0, nfb = 0;
     bool aborted = false;
+    const bool inner = (lane >= 1) && (lane <= 30);  // lanes holding results
 
     for (;;) {
         const int t = claim_tile<T, VAR>(a, lane);
@@ -544,82 +589,73 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
         const GridDesc g = a.grids[tile.grid];
         const double dt = a.run[tile.grid].dt;
         const int n = g.nx, row = tile.line0;
-        const int x0 = tile.cell0, x1 = tile.cell0 + tile.ncell;
-        const int nseg = (tile.ncell + 1) / SEG + 1;
+        const int k0 = tile.cell0, nseg = tile.ncell;
         const int bclo = g.bc[0], bchi = g.bc[1];
         const CUtensorMap* msrc = a.maps + ((size_t)tile.grid * 2 + a.src_buf) * 2 + DIR_X;
         if (lane == 0)
-            for (int c = 0; c < S && c < nseg; ++c) ring.issue(c, msrc, x0 + c * SEG, row);
+            for (int c = 0; c < S && c < nseg; ++c) ring.issue(c, msrc, -4 + STEP * (k0 + c), row);
 
         const T dtdx = T(dt / g.h);
         const T hdtdx = T(-0.5) * dtdx;
         T* __restrict__ drow = a.dst + g.off + (long long)row * g.pitch;
-
-        // carries into lane 0 of the first segment: cells x0-2 and x0-1
-        Prim<T> cWA, cWB, cWR;
-        T cirB;
-        {
-            const Cons<T> um2 = (x0 >= 2) ? global_cell<T, DIR_X>(a.src, g, row, x0 - 2)
-                                          : ghost_cell<T, DIR_X>(a.src, g, row, x0 - 2, n, bclo, bchi);
-            const Cons<T> um1 = (x0 >= 1) ? global_cell<T, DIR_X>(a.src, g, row, x0 - 1)
-                                          : ghost_cell<T, DIR_X>(a.src, g, row, x0 - 1, n, bclo, bchi);
-            cWA = cons_to_prim(K, um2);
-            cWB = cons_to_prim(K, um1, cirB);
-            cWR = cWB;  // right face of x0-2: only feeds outputs before x0
-        }
-        Cons<T> cF = {T(0), T(0), T(0), T(0)};
         T smax = T(0);
         unsigned tbad = 0;
         bool redo = false;
 
-        for (int sgi = 0; sgi < nseg; ++sgi) {
-            const int x = x0 + sgi * SEG;
-            const int sl = sgi % S;
+        for (int c = 0; c < nseg; ++c) {
+            const int x = -4 + STEP * (k0 + c);
+            const int sl = c % S;
             if (!ring.wait(sl, lane)) { aborted = true; break; }
-            const unsigned char* cur = ring.slot(sl);
             const int A = x + 2 * lane;
             Cons<T> uA, uB;
-            read_pair<T>(cur, 2 * lane, uA, uB);
-            if (x + SEG > n) {
-                // positions n and n+1 are boundary cells; beyond them nothing is used
-                if (A == n || A == n + 1) uA = ghost_cell<T, DIR_X>(a.src, g, row, A, n, bclo, bchi);
-                if (A + 1 == n || A + 1 == n + 1) uB = ghost_cell<T, DIR_X>(a.src, g, row, A + 1, n, bclo, bchi);
+            read_pair<T>(ring.slot(sl), 2 * lane, uA, uB);
+            __syncwarp();
+            if (lane == 0 && c + S < nseg) {
+                fence_proxy_async_smem();
+                ring.issue(sl, msrc, -4 + STEP * (k0 + c + S), row);
+            }
+            if (x < 0 || x + SEG > n) {
+                // positions -2, -1 and n, n+1 are boundary cells; the rest of
+                // the zero-filled positions outside the row feed no result
+                if (A == -2 || A == -1 || A == n || A == n + 1)
+                    uA = ghost_cell<T, DIR_X>(a.src, g, row, A, n, bclo, bchi);
+                if (A + 1 == -2 || A + 1 == -1 || A + 1 == n || A + 1 == n + 1)
+                    uB = ghost_cell<T, DIR_X>(a.src, g, row, A + 1, n, bclo, bchi);
             }
             T irA, irB;
             const Prim<T> WA = cons_to_prim(K, uA, irA);
             const Prim<T> WB = cons_to_prim(K, uB, irB);
-            const Prim<T> Wm2 = from_left(WA, cWA, lane);   // cell A-2
-            const Prim<T> Wm1 = from_left(WB, cWB, lane);   // cell A-1
-            const T irm1 = from_left(irB, cirB, lane);
-            Prim<T> WL1, WR1, WL2, WR2;
-            trace(K, hdtdx, Wm2, Wm1, irm1, WA, WL1, WR1);  // cell A-1
-            trace(K, hdtdx, Wm1, WA, irA, WB, WL2, WR2);    // cell A
-            const Prim<T> WRm = from_left(WR2, cWR, lane);  // right face of A-2
+            // lanes 0 and 31 have no left / right neighbour in the segment and
+            // hold no result; they mirror their own cells so their throw-away
+            // Riemann problems stay mild and do not stretch the warp's Newton loop
+            Prim<T> Wm = shfl_up1(WB);    // cell A-1
+            Prim<T> Wp = shfl_down1(WA);  // cell B+1
+            if (lane == 0) Wm = WA;
+            if (lane == 31) Wp = WB;
+            Prim<T> WLA, WRA, WLB, WRB;
+            trace(K, hdtdx, Wm, WA, irA, WB, WLA, WRA);  // cell A
+            trace(K, hdtdx, WA, WB, irB, Wp, WLB, WRB);  // cell B
+            Prim<T> WRm = shfl_up1(WRB);  // right face of A-1
+            if (lane == 0) WRm = WLA;
             bool r1 = false, r2 = false;
-            const Cons<T> F1 = FluxOp<T, VAR>::eval(a, WRm, WL1, r1, nfb);  // (A-2)+1/2
-            const Cons<T> F2 = FluxOp<T, VAR>::eval(a, WR1, WL2, r2, nfb);  // (A-1)+1/2
-            const Cons<T> F0 = from_left(F2, cF, lane);     // (A-3)+1/2
-            // old states of A-2, A-1 (lane 0: the previous segment's last two)
-            Cons<T> o2, o1;
-            if (lane > 0) read_pair<T>(cur, 2 * lane - 2, o2, o1);
-            else read_pair<T>(ring.slot(sgi > 0 ? (sgi - 1) % S : sl), SEG - 2, o2, o1);
-            const Cons<T> n2 = update(o2, dtdx, F1, F0);
-            const Cons<T> n1 = update(o1, dtdx, F2, F1);
-            const bool lo = (A - 2 >= x0) && (A - 2 < x1);
-            const bool hi = (A - 1 >= x0) && (A - 1 < x1);
+            const Cons<T> Fm = FluxOp<T, VAR>::eval(a, WRm, WLA, r1, nfb);  // A - 1/2
+            const Cons<T> Fc = FluxOp<T, VAR>::eval(a, WRA, WLB, r2, nfb);  // A + 1/2
+            const Cons<T> Fp = shfl_down1(Fm);                              // B + 1/2
+            const Cons<T> nA = update(uA, dtdx, Fc, Fm);
+            const Cons<T> nB = update(uB, dtdx, Fp, Fc);
+            const bool lo = inner && A >= 0 && A < n;
+            const bool hi = inner && A + 1 < n;
             // a second-pass request counts only for interfaces feeding stored cells
-            redo |= (r1 && (lo || hi)) || (r2 && (hi || (A >= x0 && A < x1)));
+            redo |= (r1 || r2) && lo;
             if (lo) {
-                store_pair<T>(drow + (A - 2), g.plane, n2, n1, lo, hi);
-                check_cell<T, WHICH>(K, n2, tbad, smax);
-                if (hi) check_cell<T, WHICH>(K, n1, tbad, smax);
+                store_pair<T>(drow + A, g.plane, nA, nB, lo, hi);
+                check_cell<T, WHICH>(K, nA, tbad, smax);
+                if (hi) check_cell<T, WHICH>(K, nB, tbad, smax);
             }
-            __syncwarp();
-            // the previous segment's slot is free now
-            if (lane == 0 && sgi >= 1 && sgi - 1 + S < nseg) {
-                fence_proxy_async_smem();
-                ring.issue((sgi - 1) % S, msrc, x0 + (sgi - 1 + S) * SEG, row);
-            }
+            // the flux at B+1/2 (from lane l+1) feeds B: ask for a second pass
+            // there too when lane l+1 solved it in FP32 near vacuum
+            const bool r1n = __shfl_down_sync(0xffffffffu, r1, 1);
+            redo |= r1n && lo && hi;
         }
         if (aborted) break;
         finish_tile<T, VAR, WHICH>(a, t, tile.grid, acc, redo, tbad, smax, kbad, lane);

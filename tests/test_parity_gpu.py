@@ -99,7 +99,7 @@ def test_ragged_sizes_and_mixed_boundaries(nx, ny, bc, tile):
     pb = pr.random_modes(nx, ny, seed=nx * 1000 + ny)
     pb.bc = bc
     want, _, _ = O.run(pb.U, pb.h, pb.bc, 8)
-    got, _, _ = gpu_run(pb, 8, tuning=dict(tile_len=tile, span_len=64 * (1 + tile % 3)))
+    got, _, _ = gpu_run(pb, 8, tuning=dict(tile_len=tile, span_len=60 * (1 + tile % 3)))
     assert rel_err(got, want) <= TOL64
 
 
@@ -127,8 +127,8 @@ def test_results_identical_for_every_tile_shape_schedule_and_graph(precision):
     pb = pr.random_modes(150, 97, seed=21)
     pb.bc = (P_, P_, R_, R_)
     ref, _, _ = gpu_run(pb, 22, precision=precision,
-                        tuning=dict(tile_len=64, ctas_per_sm=0, graph_steps=20, span_len=64), record=False)
-    for tl, cps, gs, sl in [(4, 0, 0, 128), (8, 1, 2, 192), (16, 3, 20, 64), (100, 0, 10, 4096),
+                        tuning=dict(tile_len=64, ctas_per_sm=0, graph_steps=20, span_len=60), record=False)
+    for tl, cps, gs, sl in [(4, 0, 0, 120), (8, 1, 2, 180), (16, 3, 20, 60), (100, 0, 10, 4080),
                             (4096, 2, 0, 0), (0, 0, 20, 0)]:
         got, _, _ = gpu_run(pb, 22, precision=precision,
                             tuning=dict(tile_len=tl, ctas_per_sm=cps, graph_steps=gs, span_len=sl),
@@ -154,7 +154,7 @@ def test_fp32_second_pass_results_independent_of_tiling_and_batching():
     outs = {}
     for tl in (4, 16, 0):
         with H.Context(grids, precision=32) as c:
-            c.set_tuning(tile_len=tl, span_len={4: 64, 16: 128, 0: 0}[tl])
+            c.set_tuning(tile_len=tl, span_len={4: 60, 16: 120, 0: 0}[tl])
             for g, p in enumerate(pbs):
                 c.set_state(g, p.U)
             c.step(5, dt_override=dts)
