@@ -312,6 +312,33 @@ struct YWalk {
     Cons<T> flo;      // flux at (k-2) - 1/2
 };
 
+// this lane's cell j (row kc + j) of a y chunk in shared memory
+template <class T>
+__device__ __forceinline__ Cons<T> chunk_cell(const T* sp, int j, int lane) {
+    constexpr int C = 4;
+    return Cons<T>{sp[(0 * C + j) * 32 + lane], sp[(2 * C + j) * 32 + lane], sp[(1 * C + j) * 32 + lane],
+                   sp[(3 * C + j) * 32 + lane]};
+}
+
+// Boundary cell at row k (k in {-2, -1, n, n+1}) of a y walk.  Reflective /
+// transmissive: the mirror rows 1, 0 are in the first chunk (rows -2..1), the
+// mirror rows n-1, n-2 are the walk's last two conserved states (n-2 is saved
+// when row n is formed); periodic: the wrap-around row from global memory.
+template <class T>
+__device__ __forceinline__ Cons<T> y_ghost(const T* __restrict__ src, const GridDesc& g, int col, int k, int n,
+                                           int bclo, int bchi, const T* sp, int kc, int lane,
+                                           const YWalk<T>& w, Cons<T>& gsave) {
+    const int bc = (k < 0) ? bclo : bchi;
+    if (bc == BC_PERIODIC) return global_cell<T, DIR_Y>(src, g, col, (k < 0) ? k + n : k - n);
+    const bool f = (bc == BC_REFLECT);
+    if (k < 0) return flip(chunk_cell<T>(sp, -1 - k - kc, lane), f);
+    if (k == n) {
+        gsave = flip(w.u0, f);
+        return flip(w.u1, f);
+    }
+    return gsave;
+}
+
 template <class T, int VAR, int WHICH>
 __device__ __forceinline__ void y_step(const SweepArgs<T>& a, YWalk<T>& s, const Cons<T>& u, T dtdx, T hdtdx,
                                        bool& redo, unsigned& nfb, T* __restrict__ d, long long plane, bool valid,
@@ -376,6 +403,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
         const T hdtdx = T(-0.5) * dtdx;
         T* __restrict__ dcol = a.dst + g.off + line;
         YWalk<T> w = {};
+        Cons<T> gsave = {};  // mirror of row n-2, kept for position n+1
         T smax = T(0);
         unsigned tbad = 0;
         bool redo = false;
@@ -393,9 +421,8 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                 for (int j = 0; j < C; ++j) {
                     const int k = kc + j;
                     if (k > klast) break;
-                    Cons<T> u = Cons<T>{sp[(0 * C + j) * 32 + lane], sp[(2 * C + j) * 32 + lane],
-                                        sp[(1 * C + j) * 32 + lane], sp[(3 * C + j) * 32 + lane]};
-                    if (k < 0 || k >= n) u = ghost_cell<T, DIR_Y>(a.src, g, lsafe, k, n, bclo, bchi);
+                    Cons<T> u = chunk_cell<T>(sp, j, lane);
+                    if (k < 0 || k >= n) u = y_ghost<T>(a.src, g, lsafe, k, n, bclo, bchi, sp, kc, lane, w, gsave);
                     if (k == s0 - 2) {
                         w.u0 = u;
                         w.w0 = cons_to_prim(K, u);
@@ -447,7 +474,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                     const int k = kc + j;
                     if (k > klast) break;
                     Cons<T> u = cell[j];
-                    if (k < 0 || k >= n) u = ghost_cell<T, DIR_Y>(a.src, g, lsafe, k, n, bclo, bchi);
+                    if (k < 0 || k >= n) u = y_ghost<T>(a.src, g, lsafe, k, n, bclo, bchi, sp, kc, lane, w, gsave);
                     if (k == s0 - 2) {
                         w.u0 = u;
                         w.w0 = cons_to_prim(K, u);
@@ -522,6 +549,11 @@ template <class T>
 __device__ __forceinline__ Prim<T> shfl_down1(const Prim<T>& v) {
     return Prim<T>{__shfl_down_sync(0xffffffffu, v.r, 1), __shfl_down_sync(0xffffffffu, v.u, 1),
                    __shfl_down_sync(0xffffffffu, v.v, 1), __shfl_down_sync(0xffffffffu, v.p, 1)};
+}
+template <class T>
+__device__ __forceinline__ Cons<T> shfl_idx(const Cons<T>& v, int src) {
+    return Cons<T>{__shfl_sync(0xffffffffu, v.r, src), __shfl_sync(0xffffffffu, v.mn, src),
+                   __shfl_sync(0xffffffffu, v.mt, src), __shfl_sync(0xffffffffu, v.E, src)};
 }
 template <class T>
 __device__ __forceinline__ Cons<T> shfl_down1(const Cons<T>& v) {
@@ -615,12 +647,35 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
                 ring.issue(sl, msrc, -4 + STEP * (k0 + c + S), row);
             }
             if (x < 0 || x + SEG > n) {
-                // positions -2, -1 and n, n+1 are boundary cells; the rest of
-                // the zero-filled positions outside the row feed no result
-                if (A == -2 || A == -1 || A == n || A == n + 1)
-                    uA = ghost_cell<T, DIR_X>(a.src, g, row, A, n, bclo, bchi);
-                if (A + 1 == -2 || A + 1 == -1 || A + 1 == n || A + 1 == n + 1)
-                    uB = ghost_cell<T, DIR_X>(a.src, g, row, A + 1, n, bclo, bchi);
+                // positions -2, -1 and n, n+1 are boundary cells.  Reflective /
+                // transmissive: the mirror cells 1, 0 or n-1, n-2 lie in this
+                // segment, so they come by shuffle; periodic: the wrap-around
+                // cells come from global memory.
+                const int kA = A, kB = A + 1;
+                const bool gA = (kA >= -2 && kA < 0) || (kA >= n && kA <= n + 1);
+                const bool gB = (kB >= -2 && kB < 0) || (kB >= n && kB <= n + 1);
+                const int bcA = (kA < 0) ? bclo : bchi, bcB = (kB < 0) ? bclo : bchi;
+                const bool mA = gA && bcA != BC_PERIODIC, mB = gB && bcB != BC_PERIODIC;
+                const int sA = mA ? ((kA < 0) ? -1 - kA : 2 * n - 1 - kA) - x : 2 * lane;
+                const int sB = mB ? ((kB < 0) ? -1 - kB : 2 * n - 1 - kB) - x : 2 * lane + 1;
+                const Cons<T> a0 = shfl_idx(uA, sA >> 1), a1 = shfl_idx(uB, sA >> 1);
+                const Cons<T> b0 = shfl_idx(uA, sB >> 1), b1 = shfl_idx(uB, sB >> 1);
+                if (mA) uA = flip((sA & 1) ? a1 : a0, bcA == BC_REFLECT);
+                else if (gA) uA = ghost_cell<T, DIR_X>(a.src, g, row, kA, n, bclo, bchi);
+                if (mB) uB = flip((sB & 1) ? b1 : b0, bcB == BC_REFLECT);
+                else if (gB) uB = ghost_cell<T, DIR_X>(a.src, g, row, kB, n, bclo, bchi);
+                // positions beyond the boundary cells (zero-filled) take a copy
+                // of the nearest boundary cell: they feed no result, and equal
+                // states keep their throw-away Riemann problems trivial
+                const int lo2 = -2 - x, hi2 = n + 1 - x;  // segment positions of -2, n+1
+                const int pl = (lo2 > 0) ? lo2 : 0, ph = (hi2 < SEG - 1) ? hi2 : SEG - 1;
+                const Cons<T> cl0 = shfl_idx(uA, pl >> 1), cl1 = shfl_idx(uB, pl >> 1);
+                const Cons<T> ch0 = shfl_idx(uA, ph >> 1), ch1 = shfl_idx(uB, ph >> 1);
+                const Cons<T> cl = (pl & 1) ? cl1 : cl0, ch = (ph & 1) ? ch1 : ch0;
+                if (kA < -2) uA = cl;
+                if (kB < -2) uB = cl;
+                if (kA > n + 1) uA = ch;
+                if (kB > n + 1) uB = ch;
             }
             T irA, irB;
             const Prim<T> WA = cons_to_prim(K, uA, irA);
