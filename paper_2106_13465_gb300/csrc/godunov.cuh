@@ -114,11 +114,10 @@ __device__ __forceinline__ double minmod(double a, double b) {
     const long long m = __double_as_longlong(fmin(fabs(a), fabs(b))) | (ia & (long long)0x8000000000000000ull);
     return take ? __longlong_as_double(m) : 0.0;
 }
+// FP32: the sign test through the product (0 when it underflows, i.e. both
+// slopes below ~1e-19 in magnitude), then the argument of smaller magnitude.
 __device__ __forceinline__ float minmod(float a, float b) {
-    const int ia = __float_as_int(a), ib = __float_as_int(b);
-    const bool take = ((ia ^ ib) >= 0) && ((ia << 1) != 0) && ((ib << 1) != 0);
-    const int m = __float_as_int(fminf(fabsf(a), fabsf(b))) | (ia & (int)0x80000000u);
-    return take ? __int_as_float(m) : 0.0f;
+    return (a * b > 0.0f) ? ((fabsf(a) < fabsf(b)) ? a : b) : 0.0f;
 }
 
 // x > 0 for x not NaN (positive finite or +inf), tested on the bit pattern.

@@ -293,7 +293,7 @@ __device__ __forceinline__ Cons<T> update(const Cons<T>& u, T dtdx, const Cons<T
 
 template <class T, int VAR, int DIR>
 struct MinBlocks { static constexpr int value = 1; };
-template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_Y> { static constexpr int value = 4; };
+template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_Y> { static constexpr int value = 6; };
 template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_X> { static constexpr int value = 6; };
 template <> struct MinBlocks<double, VAR_F64, DIR_Y> { static constexpr int value = 3; };
 template <> struct MinBlocks<double, VAR_F64, DIR_X> { static constexpr int value = 3; };
@@ -337,31 +337,6 @@ __device__ __forceinline__ Cons<T> y_ghost(const T* __restrict__ src, const Grid
         return flip(w.u1, f);
     }
     return gsave;
-}
-
-template <class T, int VAR, int WHICH>
-__device__ __forceinline__ void y_step(const SweepArgs<T>& a, YWalk<T>& s, const Cons<T>& u, T dtdx, T hdtdx,
-                                       bool& redo, unsigned& nfb, T* __restrict__ d, long long plane, bool valid,
-                                       unsigned& tbad, T& smax) {
-    // position k arrives: trace cell k-1, solve interface k-2 | k-1, update cell k-2
-    constexpr int PN = 2, PT = 1;
-    T ir2;
-    const Prim<T> w2 = cons_to_prim(a.K, u, ir2);
-    Prim<T> wl1, wr1;
-    trace(a.K, hdtdx, s.w0, s.w1, s.ir1, w2, wl1, wr1);
-    const Cons<T> fhi = FluxOp<T, VAR>::eval(a, s.wr0, wl1, redo, nfb);
-    const Cons<T> out = update(s.u0, dtdx, fhi, s.flo);
-    if (valid) {
-        d[0] = out.r;
-        d[PN * plane] = out.mn;
-        d[PT * plane] = out.mt;
-        d[3 * plane] = out.E;
-        check_cell<T, WHICH>(a.K, out, tbad, smax);
-    }
-    s.flo = fhi;
-    s.u0 = s.u1; s.u1 = u;
-    s.w0 = s.w1; s.w1 = w2; s.ir1 = ir2;
-    s.wr0 = wr1;
 }
 
 template <class T, int VAR, int WHICH>
@@ -413,96 +388,46 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
             if (!ring.wait(sl, lane)) { aborted = true; break; }
             const T* sp = reinterpret_cast<const T*>(ring.slot(sl));
             const int kc = kfirst + c * C;
-            if (sizeof(T) == 8) {
-                // FP64: one copy of the per-cell arithmetic (the FP64 pipe,
-                // not issue, bounds this kernel; a small loop body keeps the
-                // instruction cache warm), warm-up and edges as uniform branches
-#pragma unroll 1
-                for (int j = 0; j < C; ++j) {
-                    const int k = kc + j;
-                    if (k > klast) break;
-                    Cons<T> u = chunk_cell<T>(sp, j, lane);
-                    if (k < 0 || k >= n) u = y_ghost<T>(a.src, g, lsafe, k, n, bclo, bchi, sp, kc, lane, w, gsave);
-                    if (k == s0 - 2) {
-                        w.u0 = u;
-                        w.w0 = cons_to_prim(K, u);
-                        continue;
-                    }
-                    T ir2;
-                    const Prim<T> w2 = cons_to_prim(K, u, ir2);
-                    if (k > s0 - 1) {
-                        Prim<T> wl1, wr1;
-                        trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
-                        Cons<T> fhi = w.flo;
-                        if (k > s0) fhi = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb);
-                        if (k > s0 + 1) {
-                            const Cons<T> out = update(w.u0, dtdx, fhi, w.flo);
-                            if (valid) {
-                                T* d = dcol + (long long)(k - 2) * g.pitch;
-                                d[0] = out.r;
-                                d[2 * g.plane] = out.mn;
-                                d[1 * g.plane] = out.mt;
-                                d[3 * g.plane] = out.E;
-                                check_cell<T, WHICH>(K, out, tbad, smax);
-                            }
+            // one copy of the per-cell arithmetic: a small loop body keeps the
+            // instruction cache warm and the register count low; warm-up and
+            // boundary positions are uniform branches
+            #pragma unroll 1
+            for (int j = 0; j < C; ++j) {
+                const int k = kc + j;
+                if (k > klast) break;
+                Cons<T> u = chunk_cell<T>(sp, j, lane);
+                if (k < 0 || k >= n) u = y_ghost<T>(a.src, g, lsafe, k, n, bclo, bchi, sp, kc, lane, w, gsave);
+                if (k == s0 - 2) {
+                    w.u0 = u;
+                    w.w0 = cons_to_prim(K, u);
+                    continue;
+                }
+                T ir2;
+                const Prim<T> w2 = cons_to_prim(K, u, ir2);
+                if (k > s0 - 1) {
+                    Prim<T> wl1, wr1;
+                    trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
+                    Cons<T> fhi = w.flo;
+                    if (k > s0) fhi = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb);
+                    if (k > s0 + 1) {
+                        const Cons<T> out = update(w.u0, dtdx, fhi, w.flo);
+                        if (valid) {
+                            T* d = dcol + (long long)(k - 2) * g.pitch;
+                            d[0] = out.r;
+                            d[2 * g.plane] = out.mn;
+                            d[1 * g.plane] = out.mt;
+                            d[3 * g.plane] = out.E;
+                            check_cell<T, WHICH>(K, out, tbad, smax);
                         }
-                        w.flo = fhi;
-                        w.u0 = w.u1;
-                        w.w0 = w.w1;
-                        w.wr0 = wr1;
                     }
-                    w.u1 = u;
-                    w.w1 = w2;
-                    w.ir1 = ir2;
+                    w.flo = fhi;
+                    w.u0 = w.u1;
+                    w.w0 = w.w1;
+                    w.wr0 = wr1;
                 }
-            } else {
-            Cons<T> cell[C];
-#pragma unroll
-            for (int j = 0; j < C; ++j)
-                cell[j] = Cons<T>{sp[(0 * C + j) * 32 + lane], sp[(2 * C + j) * 32 + lane],
-                                  sp[(1 * C + j) * 32 + lane], sp[(3 * C + j) * 32 + lane]};
-            if (c > 0 && kc + C - 1 < n && kc + C - 1 <= klast) {
-                // steady state: four interior positions, each completes a row
-#pragma unroll
-                for (int j = 0; j < C; ++j)
-                    y_step<T, VAR, WHICH>(a, w, cell[j], dtdx, hdtdx, redo, nfb,
-                                          dcol + (long long)(kc + j - 2) * g.pitch, g.plane, valid, tbad, smax);
-            } else {
-                // warm-up chunk or a chunk reaching past the line or the tile
-#pragma unroll
-                for (int j = 0; j < C; ++j) {
-                    const int k = kc + j;
-                    if (k > klast) break;
-                    Cons<T> u = cell[j];
-                    if (k < 0 || k >= n) u = y_ghost<T>(a.src, g, lsafe, k, n, bclo, bchi, sp, kc, lane, w, gsave);
-                    if (k == s0 - 2) {
-                        w.u0 = u;
-                        w.w0 = cons_to_prim(K, u);
-                    } else if (k == s0 - 1) {
-                        w.u1 = u;
-                        w.w1 = cons_to_prim(K, u, w.ir1);
-                    } else if (k == s0) {
-                        T ir2;
-                        const Prim<T> w2 = cons_to_prim(K, u, ir2);
-                        Prim<T> wl1;
-                        trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, w.wr0);
-                        w.u0 = w.u1; w.u1 = u;
-                        w.w0 = w.w1; w.w1 = w2; w.ir1 = ir2;
-                    } else if (k == s0 + 1) {
-                        T ir2;
-                        const Prim<T> w2 = cons_to_prim(K, u, ir2);
-                        Prim<T> wl1, wr1;
-                        trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);
-                        w.flo = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb);
-                        w.u0 = w.u1; w.u1 = u;
-                        w.w0 = w.w1; w.w1 = w2; w.ir1 = ir2;
-                        w.wr0 = wr1;
-                    } else {
-                        y_step<T, VAR, WHICH>(a, w, u, dtdx, hdtdx, redo, nfb,
-                                              dcol + (long long)(k - 2) * g.pitch, g.plane, valid, tbad, smax);
-                    }
-                }
-            }
+                w.u1 = u;
+                w.w1 = w2;
+                w.ir1 = ir2;
             }
             __syncwarp();
             if (lane == 0 && c + S < nch) {
