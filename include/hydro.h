@@ -53,7 +53,8 @@ enum { HYDRO_BC_REFLECT = 0, HYDRO_BC_TRANSMISSIVE = 1, HYDRO_BC_PERIODIC = 2 };
 
 enum { HYDRO_PREC_FP32 = 32, HYDRO_PREC_FP64 = 64 };
 
-/* One grid: nx * ny interior cells (each >= 2), square cells of side h > 0,
+/* One grid: nx * ny interior cells (each in [2, 2^24], and ny times nx
+ * rounded up to a multiple of 32 below 2^31), square cells of side h > 0,
  * boundary conditions bc[] = {x low, x high, y low, y high}. */
 typedef struct {
     int nx, ny;

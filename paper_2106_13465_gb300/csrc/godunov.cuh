@@ -19,6 +19,10 @@
 
 namespace hydro {
 
+// Terms of the binomial series of (1 + x)^z used for |x| <= kBinomRadius.
+constexpr int kBinomTerms = 8;
+constexpr double kBinomRadius = 0.01;
+
 // Constants of the scheme in the arithmetic type, derived once on the host.
 template <class T>
 struct Consts {
@@ -41,6 +45,7 @@ struct Consts {
     T pmin;       // smallest pressure of the Riemann iteration, rho_floor * cf2g
     T tol;        // Newton convergence test |p_new - p| <= tol * p_new
     int niter;    // maximum Newton iterations
+    T bz[kBinomTerms];  // binomial coefficients C(z, k), k = 1 .. kBinomTerms
 };
 
 template <class T> struct Prim { T r, u, v, p; };     // u normal, v tangential
@@ -63,10 +68,26 @@ __device__ __forceinline__ float tabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
 
-// x^e with the exact value 1 for x == 1 (pow(1, e) = 1 for every e).
+// (p / p_K)^z, given 1/p_K.  FP64: where x = (p - p_K)/p_K has |x| <= 0.01,
+// the binomial series (1 + x)^z = sum_k C(z, k) x^k summed to k = 8 by
+// Horner's rule; for 0 < z < 1/2 the remainder is below 0.5 * 0.01^9, far
+// under one unit in the last place; p = p_K gives 1 exactly.  This is the
+// common case of the Newton iteration (iterates near p_K) and costs 8 fused
+// multiply-adds instead of a logarithm and an exponential.  Farther from 1,
+// and in FP32 (where the power is two hardware approximations), exp2/log2.
 template <class T>
-__device__ __forceinline__ T pow_or_one(T x, T e) {
-    return (x == T(1)) ? T(1) : tpow(x, e);
+__device__ __forceinline__ T pow_z(const Consts<T>& K, T p, T pK, T ip) {
+    if (p == pK) return T(1);
+    if (sizeof(T) == 8) {
+        const T x = (p - pK) * ip;
+        if (tabs(x) <= T(kBinomRadius)) {
+            T s = K.bz[kBinomTerms - 1];
+#pragma unroll
+            for (int k = kBinomTerms - 2; k >= 0; --k) s = tfma(s, x, K.bz[k]);
+            return tfma(s, x, T(1));
+        }
+    }
+    return tpow(p * ip, K.z);
 }
 
 // ------------------------------------------------------------- EOS -----
@@ -223,9 +244,7 @@ __device__ __forceinline__ void pressure_fn(const Consts<T>& K, const Side<T>& s
         b = q * tfma(T(-0.5) * dpk, q * q * s.iA, T(1));
         pz = T(-1);
     } else {
-        const bool one = (p == s.p);
-        const T r = one ? T(1) : p * s.ip;
-        pz = one ? T(1) : tpow(r, K.z);
+        pz = pow_z(K, p, s.p, s.ip);
         f = tfma(s.cG4, pz, -s.cG4);
         a = pz * s.irc * s.p;
         b = T(0);
@@ -316,7 +335,7 @@ __device__ __forceinline__ Prim<T> sample_side(const Consts<T>& K, const Side<T>
         const T hk = sgn * S.u - S.c;                              // head
         if (T(0) <= hk) { W.r = S.r; W.u = S.u; W.p = S.p; }
         else {
-            if (pz < T(0)) pz = one ? T(1) : tpow(pr, K.z);
+            if (pz < T(0)) pz = pow_z(K, st.p, S.p, S.ip);
             const T tk = tfma(-S.c, pz, sgn * st.u);               // tail
             if (T(0) > tk) {
                 W.r = one ? S.r : S.r * pr / (pz * pz);

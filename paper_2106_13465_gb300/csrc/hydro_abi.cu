@@ -52,6 +52,11 @@ Consts<T> make_consts(const hydro_params& p, double tol) {
     K.pmin = (T)(p.rho_floor * (p.c_floor * p.c_floor / g));
     K.tol = (T)tol;
     K.niter = p.niter_riemann;
+    double c = 1.0, z = (g - 1.0) / (2.0 * g);
+    for (int k = 1; k <= kBinomTerms; ++k) {
+        c *= (z - (k - 1)) / k;  // C(z, k)
+        K.bz[k - 1] = (T)c;
+    }
     return K;
 }
 
@@ -142,6 +147,11 @@ hydro_status validate_params(const hydro_params* p) {
         char buf[160];
         if (G.nx < 2 || G.ny < 2 || G.nx > (1 << 24) || G.ny > (1 << 24)) {
             snprintf(buf, sizeof buf, "grid %d: nx, ny must be in [2, 2^24] (got %d x %d)", g, G.nx, G.ny);
+            return fail(nullptr, HYDRO_EINVAL, buf);
+        }
+        // the y sweep addresses a column of a plane with 32-bit offsets
+        if ((long long)round_up(G.nx, 32) * G.ny >= (1LL << 31)) {
+            snprintf(buf, sizeof buf, "grid %d: a plane (ny x nx rounded up to 32) must hold fewer than 2^31 cells", g);
             return fail(nullptr, HYDRO_EINVAL, buf);
         }
         if (!(G.h > 0.0) || !std::isfinite(G.h)) {

@@ -293,7 +293,7 @@ __device__ __forceinline__ Cons<T> update(const Cons<T>& u, T dtdx, const Cons<T
 
 template <class T, int VAR, int DIR>
 struct MinBlocks { static constexpr int value = 1; };
-template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_Y> { static constexpr int value = 6; };
+template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_Y> { static constexpr int value = 5; };
 template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_X> { static constexpr int value = 6; };
 template <> struct MinBlocks<double, VAR_F64, DIR_Y> { static constexpr int value = 3; };
 template <> struct MinBlocks<double, VAR_F64, DIR_X> { static constexpr int value = 3; };
@@ -376,7 +376,13 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
 
         const T dtdx = T(dt / g.h);
         const T hdtdx = T(-0.5) * dtdx;
-        T* __restrict__ dcol = a.dst + g.off + line;
+        // this lane's column in the four output planes (normal momentum is
+        // plane 2); a plane holds fewer than 2^31 elements (checked on the host)
+        T* __restrict__ q0 = a.dst + g.off + lsafe;
+        T* __restrict__ qn = q0 + 2 * g.plane;
+        T* __restrict__ qt = q0 + g.plane;
+        T* __restrict__ qe = q0 + 3 * g.plane;
+        const unsigned pitch = (unsigned)g.pitch;
         YWalk<T> w = {};
         Cons<T> gsave = {};  // mirror of row n-2, kept for position n+1
         T smax = T(0);
@@ -388,43 +394,52 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
             if (!ring.wait(sl, lane)) { aborted = true; break; }
             const T* sp = reinterpret_cast<const T*>(ring.slot(sl));
             const int kc = kfirst + c * C;
-            // one copy of the per-cell arithmetic: a small loop body keeps the
-            // instruction cache warm and the register count low; warm-up and
-            // boundary positions are uniform branches
+            int j0 = 0;
+            if (c == 0) {
+                // positions s0-2 and s0-1 only fill the window (both < n - 1;
+                // below 0 they mirror rows of this chunk or wrap around)
+                Cons<T> u = chunk_cell<T>(sp, 0, lane);
+                if (kc < 0) u = y_ghost<T>(a.src, g, lsafe, kc, n, bclo, bchi, sp, kc, lane, w, gsave);
+                w.u0 = u;
+                w.w0 = cons_to_prim(K, u);
+                u = chunk_cell<T>(sp, 1, lane);
+                if (kc + 1 < 0) u = y_ghost<T>(a.src, g, lsafe, kc + 1, n, bclo, bchi, sp, kc, lane, w, gsave);
+                w.u1 = u;
+                w.w1 = cons_to_prim(K, u, w.ir1);
+                j0 = 2;
+            }
+            // one copy of the per-cell arithmetic: position k completes the
+            // trace of cell k-1, the flux at (k-1)-1/2 and (from k = s0+2 on)
+            // the update of row k-2
             #pragma unroll 1
-            for (int j = 0; j < C; ++j) {
+            for (int j = j0; j < C; ++j) {
                 const int k = kc + j;
                 if (k > klast) break;
                 Cons<T> u = chunk_cell<T>(sp, j, lane);
-                if (k < 0 || k >= n) u = y_ghost<T>(a.src, g, lsafe, k, n, bclo, bchi, sp, kc, lane, w, gsave);
-                if (k == s0 - 2) {
-                    w.u0 = u;
-                    w.w0 = cons_to_prim(K, u);
-                    continue;
-                }
+                if (k >= n) u = y_ghost<T>(a.src, g, lsafe, k, n, bclo, bchi, sp, kc, lane, w, gsave);
                 T ir2;
                 const Prim<T> w2 = cons_to_prim(K, u, ir2);
-                if (k > s0 - 1) {
-                    Prim<T> wl1, wr1;
-                    trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
-                    Cons<T> fhi = w.flo;
-                    if (k > s0) fhi = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb);
-                    if (k > s0 + 1) {
-                        const Cons<T> out = update(w.u0, dtdx, fhi, w.flo);
-                        if (valid) {
-                            T* d = dcol + (long long)(k - 2) * g.pitch;
-                            d[0] = out.r;
-                            d[2 * g.plane] = out.mn;
-                            d[1 * g.plane] = out.mt;
-                            d[3 * g.plane] = out.E;
-                            check_cell<T, WHICH>(K, out, tbad, smax);
-                        }
+                Prim<T> wl1, wr1;
+                trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
+                // at k = s0 the face left of cell s0-1 is not formed: solve a
+                // trivial problem (equal states) whose flux is never used
+                if (k == s0) w.wr0 = wl1;
+                const Cons<T> fhi = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb);
+                if (k >= s0 + 2) {
+                    const Cons<T> out = update(w.u0, dtdx, fhi, w.flo);
+                    if (valid) {
+                        const unsigned o = (unsigned)(k - 2) * pitch;
+                        q0[o] = out.r;
+                        qn[o] = out.mn;
+                        qt[o] = out.mt;
+                        qe[o] = out.E;
+                        check_cell<T, WHICH>(K, out, tbad, smax);
                     }
-                    w.flo = fhi;
-                    w.u0 = w.u1;
-                    w.w0 = w.w1;
-                    w.wr0 = wr1;
                 }
+                w.flo = fhi;
+                w.u0 = w.u1;
+                w.w0 = w.w1;
+                w.wr0 = wr1;
                 w.u1 = u;
                 w.w1 = w2;
                 w.ir1 = ir2;

@@ -47,6 +47,8 @@ def _params(**kw):
     (dict(rho_floor=0.0), "floor"),
     (dict(grids=[(1, 16, 0.1, (0, 0, 0, 0))]), "nx"),
     (dict(grids=[(16, 16, 0.0, (0, 0, 0, 0))]), "h must"),
+    (dict(grids=[(65536, 32768, 0.1, (0, 0, 0, 0))]), "2^31"),
+    (dict(grids=[(46337, 46337, 0.1, (0, 0, 0, 0))]), "2^31"),
     (dict(grids=[(16, 16, 0.1, (2, 0, 0, 0))]), "periodic"),
     (dict(grids=[(16, 16, 0.1, (0, 0, 7, 0))]), "boundary"),
 ])
