@@ -94,9 +94,18 @@ typedef struct {
  *   span_len      x sweep: results of a row per warp task (a multiple of 60:
  *                 a warp walks a row in overlapping 64-cell segments that
  *                 yield 60 results each)
- * tile_len and span_len default to the best makespan of a list-scheduling
- * model of the tile queue on the resident warps.  Results are bit-identical
- * for every admissible setting. */
+ * tile_len = 0 (default) and span_len = 0 take the tile length with the
+ * best makespan of a list-scheduling model of the tile queue on the
+ * resident warps (uniform cost per cell).  In FP64 contexts tile_len = 0
+ * also makes the y tiles adaptive: every y sweep records an estimate of the
+ * work (Newton iterations, powers) spent on each block of 4 rows of each
+ * 32-column group, and before the next y sweep the library splits each
+ * model tile into pieces whose recorded work stays below the mean work
+ * of a model tile (pieces of at least half that work are queued first), so
+ * regions where the Riemann solver works harder get shorter tiles.  The
+ * tiling follows the state, not the timing.  Results
+ * are bit-identical for every admissible setting (a cell's update does not
+ * depend on the schedule). */
 typedef struct {
     int tile_len;
     int ctas_per_sm;
@@ -108,7 +117,8 @@ typedef struct {
  *   steps          completed steps
  *   riemann_fp64   FP32 contexts: interface solves redone in FP64 near vacuum
  *   status_flags   bit 0: non-positive/NaN density, bit 1: non-positive/NaN
- *                  energy, bit 2: a bounded wait timed out (sticky until
+ *                  energy, bit 2: a bounded wait timed out, bit 3: internal
+ *                  error, a tile outside its grid was skipped (sticky until
  *                  hydro_set_state) */
 typedef struct {
     long long steps;

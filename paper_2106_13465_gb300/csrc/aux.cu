@@ -30,6 +30,8 @@ __global__ void step_prologue_kernel(GridRun* run, const GridDesc* grids, int ng
         ctr->redo_count[1] = 0u;
         ctr->redo_claim[0] = 0u;
         ctr->redo_claim[1] = 0u;
+        ctr->ytiles[0] = 0u;
+        ctr->ytiles[1] = 0u;
         ctr->steps += 1ull;
     }
 }
@@ -39,6 +41,98 @@ cudaError_t launch_step_prologue(GridRun* run, const GridDesc* grids, int ngrids
                                  double* dt_log, cudaStream_t s) {
     const int nt = ngrids < 1024 ? ((ngrids + 31) / 32) * 32 : 1024;
     step_prologue_kernel<<<1, nt, 0, s>>>(run, grids, ngrids, ctr, dt_override, cfl, dt_log);
+    return cudaGetLastError();
+}
+
+// ---- adaptive y tiles ------------------------------------------------------
+// One thread per tile of the static tiling (the tiling the scheduling model
+// picks for uniform cost; every tile a whole number of cost blocks except at
+// the end of a column).  The thread walks the tile's blocks in order and
+// starts a new piece before block b when adding b would take the piece's
+// recorded work above `cap` (a piece always gets at least one block), so
+// uniform work reproduces the static tiling and the tiles where the solver
+// works harder are split.  Pieces of at least `big` work are queued first
+// (from the front of the list), the others last (from its back): the warps
+// start on the long jobs and the short ones fill the tail of the sweep.
+// Each warp reserves its threads' slots with one atomic per class.  The
+// previous step's y sweep recorded the work and its total (in the slot of
+// its step parity); this kernel clears the slot the coming y sweep fills.
+template <bool EMIT>
+__device__ __forceinline__ void split_tile(const Tile& st, const float* __restrict__ cst, float cap, float big,
+                                           Tile* __restrict__ out, int cap_tiles, unsigned& nf, unsigned& nb) {
+    const int b0 = st.cell0 / kYBlock, b1 = (st.cell0 + st.ncell + kYBlock - 1) / kYBlock;
+    const int rend = st.cell0 + st.ncell;
+    float acc = 0.0f;
+    int start = b0;
+    auto put = [&](int r0, int nrows, float work) {
+        if (work >= big) {
+            if (EMIT) out[nf] = Tile{st.grid, st.line0, r0, nrows};
+            ++nf;
+        } else {
+            if (EMIT) out[cap_tiles - 1 - (int)nb] = Tile{st.grid, st.line0, r0, nrows};
+            ++nb;
+        }
+    };
+    for (int b = b0; b < b1; ++b) {
+        const float c = cst[b];
+        if (b > start && acc + c > cap) {
+            put(start * kYBlock, (b - start) * kYBlock, acc);
+            acc = 0.0f;
+            start = b;
+        }
+        acc += c;
+    }
+    put(start * kYBlock, rend - start * kYBlock, acc);
+}
+
+__device__ __forceinline__ unsigned warp_exclusive_scan(unsigned v, int lane, unsigned& total) {
+    unsigned incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - v;
+}
+
+__global__ void retile_y_kernel(const GridDesc* __restrict__ grids, const Tile* __restrict__ stat, int nstat,
+                                const float* __restrict__ ycost, DevCounters* ctr, Tile* __restrict__ tiles,
+                                int cap_tiles, double cap_per_total, double big_per_total) {
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int lane = threadIdx.x & 31;
+    const unsigned par = (unsigned)(ctr->steps & 1ull);
+    if (i == 0) ctr->ycost_total[par] = 0ull;
+    const double total = (double)ctr->ycost_total[par ^ 1u];
+    const float cap = (float)(total * cap_per_total), big = (float)(total * big_per_total);
+    Tile st{};
+    const float* cst = nullptr;
+    unsigned nf = 0, nb = 0;
+    if (i < nstat) {
+        st = stat[i];
+        const GridDesc& g = grids[st.grid];
+        cst = ycost + g.yblk + (long long)(st.line0 / kWarpLines) * g.nrb;
+        split_tile<false>(st, cst, cap, big, tiles, cap_tiles, nf, nb);
+    }
+    // warp-aggregated reservation of the pieces' slots, one atomic per class
+    unsigned tf, tb;
+    const unsigned of = warp_exclusive_scan(nf, lane, tf), ob = warp_exclusive_scan(nb, lane, tb);
+    unsigned basef = 0, baseb = 0;
+    if (lane == 0) {
+        basef = atomicAdd(&ctr->ytiles[0], tf);
+        baseb = atomicAdd(&ctr->ytiles[1], tb);
+    }
+    basef = __shfl_sync(0xffffffffu, basef, 0) + of;
+    baseb = __shfl_sync(0xffffffffu, baseb, 0) + ob;
+    if (i < nstat) split_tile<true>(st, cst, cap, big, tiles, cap_tiles, basef, baseb);
+}
+
+cudaError_t launch_retile_y(const GridDesc* grids, const Tile* stat, int nstat, const float* ycost,
+                            DevCounters* ctr, Tile* tiles, int cap_tiles, double cap_per_total,
+                            double big_per_total, cudaStream_t s) {
+    const int threads = 128;
+    const int blocks = (nstat + threads - 1) / threads;
+    retile_y_kernel<<<blocks, threads, 0, s>>>(grids, stat, nstat, ycost, ctr, tiles, cap_tiles, cap_per_total,
+                                               big_per_total);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,7 @@ struct Consts {
     T tol;        // Newton convergence test |p_new - p| <= tol * p_new
     int niter;    // maximum Newton iterations
     T bz[kBinomTerms];  // binomial coefficients C(z, k), k = 1 .. kBinomTerms
+    T pz_series;        // (1 - kBinomRadius)^z: (p/p_K)^z below it came from exp2/log2
 };
 
 template <class T> struct Prim { T r, u, v, p; };     // u normal, v tangential
@@ -256,6 +257,7 @@ struct Star {
     T p, u;
     T pzl, pzr;    // (p*/p_K)^z of each side, -1 where not evaluated
     bool floored;  // the iterate reached the pressure floor
+    int iters;     // pressure-function evaluations of each side
 };
 
 // (p*, u*) by Newton from the PVRS estimate
@@ -275,6 +277,7 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
     const T du = R.u - L.u;
     T fl, al, bl, pzl, fr, ar, br, pzr;
     bool conv = false;
+    int iters = K.niter + 1;
     for (int it = 0; it < K.niter; ++it) {
         pressure_fn(K, L, p, fl, al, bl, pzl);
         pressure_fn(K, R, p, fr, ar, br, pzr);
@@ -294,6 +297,7 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
             }
             p = pn;
             conv = true;
+            iters = it + 1;
             break;
         }
         p = pn;
@@ -308,6 +312,7 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
     st.pzl = pzl;
     st.pzr = pzr;
     st.floored = floored;
+    st.iters = iters;
     return st;
 }
 
@@ -378,13 +383,27 @@ __device__ __forceinline__ T sound_speed(const Consts<T>& K, const Prim<T>& W) {
     return tsqrt(K.gamma * W.p / W.r);
 }
 
+// A rough count of the FP64 operations of one interface solve, used only to
+// schedule work (adaptive y tiles): a fixed part (sides, guess, sampling,
+// flux), and per evaluation of the pressure functions the Newton update and
+// both sides, where a rarefaction power far from p_K (exp2/log2) costs about
+// four times the series near it.
+template <class T>
+__device__ __forceinline__ unsigned solve_work(const Consts<T>& K, const Star<T>& s) {
+    const unsigned pl = (s.pzl > T(0) && s.pzl < K.pz_series) ? 40u : 0u;
+    const unsigned pr = (s.pzr > T(0) && s.pzr < K.pz_series) ? 40u : 0u;
+    return 100u + (unsigned)s.iters * (40u + pl + pr);
+}
+
 // Godunov flux at one interface between the traced states L | R.
 template <class T>
 __device__ __forceinline__ Cons<T> godunov_flux_exact(const Consts<T>& K, const Prim<T>& WL,
-                                                      const Prim<T>& WR, bool* floored) {
+                                                      const Prim<T>& WR, bool* floored,
+                                                      unsigned* work = nullptr) {
     const Side<T> L = make_side(K, WL), R = make_side(K, WR);
     const Star<T> s = riemann_star(K, L, R);
     if (floored) *floored = s.floored;
+    if (work) *work = solve_work(K, s);
     return physical_flux(K, sample0(K, L, R, s));
 }
 

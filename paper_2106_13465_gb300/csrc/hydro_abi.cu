@@ -57,6 +57,7 @@ Consts<T> make_consts(const hydro_params& p, double tol) {
         c *= (z - (k - 1)) / k;  // C(z, k)
         K.bz[k - 1] = (T)c;
     }
+    K.pz_series = (T)std::pow(1.0 - kBinomRadius, z);
     return K;
 }
 
@@ -91,6 +92,12 @@ struct hydro_ctx {
     size_t dt_log_cap = 0;
     CUtensorMap* d_maps = nullptr;  // [grid][buffer][dir]
     int* d_redo = nullptr;          // [2][redo_cap] FP32 second-pass tile lists
+    float* d_ycost = nullptr;       // recorded y-sweep cost per block (adaptive y tiles)
+    Tile* d_ystat = nullptr;        // static y tiling the adaptive tiles split
+    int nystat = 0;
+    long long nyblocks = 0;         // cost blocks of all grids
+    bool y_adaptive = false;        // y tiles cut from recorded costs every step
+    double y_cap = 0.0;             // adaptive y tiles: cost cap / total recorded cost
     int redo_cap = 0;
     int ctas_redo[2] = {0, 0};
     hydro_tuning tuning{kDefaultTileLen, 0, kDefaultGraphSteps, 0};
@@ -266,6 +273,27 @@ hydro_status build_tensor_maps(hydro_ctx* c) {
     return HYDRO_OK;
 }
 
+// Cost blocks before any y sweep has run: the rows each block holds (a
+// uniform cost per cell), and the same total in both parity slots.
+hydro_status init_ycost(hydro_ctx* c) {
+    std::vector<float> cost((size_t)c->nyblocks);
+    unsigned long long total = 0;
+    for (int g = 0; g < (int)c->gd.size(); ++g) {
+        const GridDesc& d = c->gd[g];
+        for (int cg = 0; cg < d.ycg; ++cg) {
+            for (int b = 0; b < d.nrb; ++b) {
+                const int rows = std::min(kYBlock, d.ny - b * kYBlock);
+                cost[(size_t)(d.yblk + (long long)cg * d.nrb + b)] = (float)rows;
+                total += (unsigned long long)rows;
+            }
+        }
+    }
+    const unsigned long long tot2[2] = {total, total};
+    HCK(c, cudaMemcpy(c->d_ycost, cost.data(), sizeof(float) * cost.size(), cudaMemcpyHostToDevice));
+    HCK(c, cudaMemcpy(&c->d_ctr->ycost_total[0], tot2, sizeof tot2, cudaMemcpyHostToDevice));
+    return HYDRO_OK;
+}
+
 hydro_status upload_tiles(hydro_ctx* c) {
     for (int d = 0; d < 2; ++d) {
         const int var = c->prec == 64 ? VAR_F64 : VAR_F32_MAIN;
@@ -276,15 +304,39 @@ hydro_status upload_tiles(hydro_ctx* c) {
         const int warps_per_cta = kSweepThreads / 32;
         const int resident_warps = c->nsm * per_sm * warps_per_cta;
         const int chosen = d == DIR_X ? c->tuning.span_len / kXStride : c->tuning.tile_len;
-        const int L = chosen > 0 ? chosen : auto_tile_len(c->gd, d, resident_warps);
-        c->tile_len_used[d] = L;
-        std::vector<Tile> t;
-        build_tiles(c->gd, d, L, t);
         if (c->d_tiles[d]) cudaFree(c->d_tiles[d]);
         c->d_tiles[d] = nullptr;
-        HCK(c, cudaMalloc(&c->d_tiles[d], sizeof(Tile) * t.size()));
-        HCK(c, cudaMemcpy(c->d_tiles[d], t.data(), sizeof(Tile) * t.size(), cudaMemcpyHostToDevice));
-        c->ntiles[d] = (int)t.size();
+        if (d == DIR_Y && chosen == 0 && c->prec == 64) {
+            // adaptive y tiles (FP64, where the cost of a cell varies most
+            // with the Riemann problems it meets): the list is cut on the
+            // device every step; it
+            // never holds more tiles than there are cost blocks.  The length
+            // cap is the model's static tile length; the cost cap a multiple
+            // of the mean cost of such a tile.
+            const int L = auto_tile_len(c->gd, d, resident_warps);
+            const int lb = std::max(kYBlock, L / kYBlock * kYBlock);  // L is a multiple of 4
+            std::vector<Tile> t;
+            build_tiles(c->gd, d, lb, t);
+            if (c->d_ystat) cudaFree(c->d_ystat);
+            c->d_ystat = nullptr;
+            HCK(c, cudaMalloc(&c->d_ystat, sizeof(Tile) * t.size()));
+            HCK(c, cudaMemcpy(c->d_ystat, t.data(), sizeof(Tile) * t.size(), cudaMemcpyHostToDevice));
+            c->nystat = (int)t.size();
+            c->y_adaptive = true;
+            c->y_cap = kYCostCap / (double)t.size();
+            c->tile_len_used[d] = 0;
+            HCK(c, cudaMalloc(&c->d_tiles[d], sizeof(Tile) * (size_t)c->nyblocks));
+            c->ntiles[d] = (int)std::min<long long>(c->nyblocks, 1LL << 30);
+        } else {
+            if (d == DIR_Y) c->y_adaptive = false;
+            const int L = chosen > 0 ? chosen : auto_tile_len(c->gd, d, resident_warps);
+            c->tile_len_used[d] = L;
+            std::vector<Tile> t;
+            build_tiles(c->gd, d, L, t);
+            HCK(c, cudaMalloc(&c->d_tiles[d], sizeof(Tile) * t.size()));
+            HCK(c, cudaMemcpy(c->d_tiles[d], t.data(), sizeof(Tile) * t.size(), cudaMemcpyHostToDevice));
+            c->ntiles[d] = (int)t.size();
+        }
         const int need = (c->ntiles[d] + warps_per_cta - 1) / warps_per_cta;
         c->ctas[d] = std::max(1, std::min(need, c->nsm * per_sm));
         if (c->prec == 32) {
@@ -321,6 +373,9 @@ SweepArgs<T> sweep_args(hydro_ctx* c, int which, const Consts<T>& K) {
     a.tiles = nullptr;
     a.maps = c->d_maps;
     a.ntiles = 0;
+    a.ngrids = (int)c->gd.size();
+    a.ntiles_dev = nullptr;
+    a.ycost = c->d_ycost;
     a.which = which;
     a.src_buf = which;
     a.redo_list = c->d_redo;
@@ -341,6 +396,11 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
     e = launch_step_prologue(c->d_run, c->d_grids, (int)c->gd.size(), c->d_ctr, ovr, c->cfl, log, s);
     if (e != cudaSuccess) return e;
+    if (c->y_adaptive) {
+        e = launch_retile_y(c->d_grids, c->d_ystat, c->nystat, c->d_ycost, c->d_ctr, c->d_tiles[DIR_Y],
+                            c->ntiles[DIR_Y], c->y_cap, c->y_cap * (kYBigJob / kYCostCap), s);
+        if (e != cudaSuccess) return e;
+    }
     if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
     const int first = parity == 0 ? DIR_X : DIR_Y;
     for (int which = 0; which < 2; ++which) {
@@ -348,6 +408,7 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
         SweepArgs<T> a = sweep_args<T>(c, which, K);
         a.tiles = c->d_tiles[dir];
         a.ntiles = c->ntiles[dir];
+        if (dir == DIR_Y && c->y_adaptive) a.ntiles_dev = c->d_ctr->ytiles;
         if (sizeof(T) == 8) {
             e = launch_sweep<T>(dir, VAR_F64, a, c->ctas[dir], s);
         } else {
@@ -401,6 +462,8 @@ template <class T>
 T* state_ptr(hydro_ctx* c) { return (T*)c->buf[0]; }
 
 hydro_status status_result(hydro_ctx* c, unsigned int status) {
+    if (status & STATUS_BAD_TILE)
+        return fail(c, HYDRO_ECUDA, "internal error: a sweep tile lies outside its grid (tile skipped)");
     if (status & STATUS_TIMEOUT)
         return fail(c, HYDRO_ETIMEOUT, "a bounded wait for a TMA copy gave up (sweep kernel)");
     if (status) {
@@ -457,6 +520,10 @@ hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
         d.off = off;
         for (int k = 0; k < 4; ++k) d.bc[k] = G.bc[k];
         d.h = G.h;
+        d.ycg = (G.nx + kWarpLines - 1) / kWarpLines;
+        d.nrb = (G.ny + kYBlock - 1) / kYBlock;
+        d.yblk = c->nyblocks;
+        c->nyblocks += (long long)d.ycg * d.nrb;
         off = round_up(off + 4 * d.plane, align_elems);
         max_cells = std::max(max_cells, (long long)G.nx * G.ny);
         max_ny = std::max(max_ny, (long long)G.ny);
@@ -494,6 +561,7 @@ hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
     if (c->prec == 32 &&
         (st = alloc((void**)&c->d_stage, sizeof(double) * 4 * max_cells, "staging")) != HYDRO_OK)
         return bail(st);
+    if ((st = alloc((void**)&c->d_ycost, sizeof(float) * c->nyblocks, "y cost blocks")) != HYDRO_OK) return bail(st);
 
     e = cudaMemcpy(c->d_grids, c->gd.data(), sizeof(GridDesc) * c->gd.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_run, 0, sizeof(GridRun) * c->gd.size());
@@ -502,6 +570,7 @@ hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
     if (e == cudaSuccess) e = cudaMemset(c->buf[1], 0, c->buf_elems * c->esz);
     if (e != cudaSuccess) { fail_cuda(c, "context set-up", e); return bail(HYDRO_ECUDA); }
     if ((st = build_tensor_maps(c)) != HYDRO_OK) return bail(st);
+    if ((st = init_ycost(c)) != HYDRO_OK) return bail(st);
     if ((st = upload_tiles(c)) != HYDRO_OK) return bail(st);
 
     *out = c;
@@ -524,6 +593,8 @@ void hydro_destroy(hydro_ctx* c) {
     cudaFree(c->d_dt_log);
     cudaFree(c->d_maps);
     cudaFree(c->d_redo);
+    cudaFree(c->d_ycost);
+    cudaFree(c->d_ystat);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -22,6 +22,20 @@
 // Work lists.  y sweep: a tile is 32 columns (one per lane) x ncell rows.
 // x sweep: a tile is a run of consecutive segments of one row, stored as
 // (grid, line0 = row, cell0 = first segment index, ncell = segments).
+//
+// Adaptive y tiles (FP64).  The rows of each column group (32 columns) are
+// divided into blocks of kYBlock rows.  Every y sweep records, per block, the
+// estimated work of the tile that covered it (per row, the largest solve_work
+// over the warp's lanes, spread evenly over the tile's blocks); before the
+// next y sweep a small kernel splits each tile of a static tiling (the one
+// the scheduling model picks for uniform cost, in whole blocks) into pieces
+// whose recorded work stays below kYCostCap times the mean work of a static
+// tile.  Uniform work keeps the static tiles; where the Riemann solver works
+// harder the tiles get shorter, so no warp is left with a tile far above the
+// average when the queue runs dry.  Pieces of at least kYBigJob times the
+// mean are queued before the others (longest jobs first, the short ones fill
+// the tail).  The work estimate depends only on the state, so the tiling of
+// a run is reproducible.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -33,13 +47,16 @@ namespace hydro {
 
 enum { BC_REFLECT = 0, BC_TRANSMISSIVE = 1, BC_PERIODIC = 2 };
 enum { DIR_X = 0, DIR_Y = 1 };
-enum { STATUS_BAD_RHO = 1u, STATUS_BAD_E = 2u, STATUS_TIMEOUT = 4u };
+enum { STATUS_BAD_RHO = 1u, STATUS_BAD_E = 2u, STATUS_TIMEOUT = 4u, STATUS_BAD_TILE = 8u };
 
 // kernel variants: FP64; FP32 main pass (tiles with a near-vacuum interface
 // are queued for a second pass); FP32 second pass (FP64 near vacuum)
 enum { VAR_F64 = 0, VAR_F32_MAIN = 1, VAR_F32_REDO = 2 };
 
 constexpr int kWarpLines = 32;      // lines per warp tile (one per lane)
+constexpr int kYBlock = 4;          // rows per cost block of the adaptive y tiles
+constexpr double kYCostCap = 1.0;   // adaptive y tile work cap / mean static tile work
+constexpr double kYBigJob = 0.5;    // adaptive y tiles queued first: work / mean static tile work
 constexpr int kSweepThreads = 128;  // threads per CTA of the sweep kernels
 
 // TMA ring geometry per warp.  x sweep: one slot holds a 64-cell segment of
@@ -62,6 +79,8 @@ struct GridDesc {
     int nx, ny, pitch;
     int bc[4];        // x low, x high, y low, y high
     double h;
+    long long yblk;   // first cost block of the grid (adaptive y tiles)
+    int ycg, nrb;     // column groups ceil(nx/32), row blocks ceil(ny/kYBlock)
 };
 
 // A warp tile: lines [line0, line0 + 32) of grid `grid`, cells
@@ -87,6 +106,10 @@ struct DevCounters {
     unsigned int redo_claim[2];  // work counters of the second pass
     unsigned long long steps;
     unsigned long long riemann_fp64;
+    unsigned int ytiles[2];               // adaptive y tiles of the current step: the
+                                          // list holds ytiles[0] long jobs from its
+                                          // front and ytiles[1] short ones from its back
+    unsigned long long ycost_total[2];    // recorded y-sweep work, by step parity
 };
 
 template <class T>
@@ -97,6 +120,10 @@ struct SweepArgs {
     const Tile* tiles;
     const CUtensorMap* maps;
     int ntiles;
+    int ngrids;
+    const unsigned int* ntiles_dev;  // adaptive y tiles: the two counts on the device
+                                     // (ntiles is then the capacity of the list)
+    float* ycost;                    // y sweep: per-block work recorded here
     int which;       // 0: first sweep of the step, 1: second (folds in CFL max)
     int src_buf;     // buffer index of src (its tensor maps)
     int* redo_list;  // [2][redo_cap] tile indices for the FP32 second pass
@@ -115,6 +142,15 @@ int sweep_ctas_per_sm(int dir, int var);
 // ---- launchers (defined in the kernel translation units) ------------------
 template <class T>
 cudaError_t launch_sweep(int dir, int var, const SweepArgs<T>& a, int nctas, cudaStream_t s);
+
+// Cut the adaptive y tiles from the recorded work: each of the nstat tiles
+// of the static tiling `stat` (whole cost blocks) is split where its pieces'
+// work would exceed cap_per_total times the total recorded work of the
+// previous y sweep; pieces of at least big_per_total times that total are
+// queued first, the rest last (list of cap_tiles slots).
+cudaError_t launch_retile_y(const GridDesc* grids, const Tile* stat, int nstat, const float* ycost,
+                            DevCounters* ctr, Tile* tiles, int cap_tiles, double cap_per_total,
+                            double big_per_total, cudaStream_t s);
 
 cudaError_t launch_step_prologue(GridRun* run, const GridDesc* grids, int ngrids,
                                  DevCounters* ctr, const double* dt_override, double cfl,

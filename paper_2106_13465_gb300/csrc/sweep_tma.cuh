@@ -105,9 +105,10 @@ struct FluxOp;
 template <>
 struct FluxOp<double, VAR_F64> {
     static __device__ __forceinline__ Cons<double> eval(const SweepArgs<double>& a, const Prim<double>& L,
-                                                        const Prim<double>& R, bool& redo, unsigned& nfb) {
+                                                        const Prim<double>& R, bool& redo, unsigned& nfb,
+                                                        unsigned& work) {
         (void)redo; (void)nfb;
-        return godunov_flux_exact(a.K, L, R, nullptr);
+        return godunov_flux_exact(a.K, L, R, nullptr, &work);
     }
 };
 
@@ -126,8 +127,9 @@ __device__ __forceinline__ bool near_vacuum_f32(const Prim<float>& L, const Prim
 template <>
 struct FluxOp<float, VAR_F32_MAIN> {
     static __device__ __forceinline__ Cons<float> eval(const SweepArgs<float>& a, const Prim<float>& L,
-                                                       const Prim<float>& R, bool& redo, unsigned& nfb) {
-        (void)nfb;
+                                                       const Prim<float>& R, bool& redo, unsigned& nfb,
+                                                       unsigned& work) {
+        (void)nfb; (void)work;
         const Side<float> SL = make_side(a.K, L), SR = make_side(a.K, R);
         const Star<float> s = riemann_star(a.K, SL, SR);
         if (near_vacuum_f32(L, R, s)) redo = true;
@@ -143,8 +145,9 @@ __device__ __noinline__ Cons<double> flux_fp64_near_vacuum(const Consts<double>*
 template <>
 struct FluxOp<float, VAR_F32_REDO> {
     static __device__ __forceinline__ Cons<float> eval(const SweepArgs<float>& a, const Prim<float>& L,
-                                                       const Prim<float>& R, bool& redo, unsigned& nfb) {
-        (void)redo;
+                                                       const Prim<float>& R, bool& redo, unsigned& nfb,
+                                                       unsigned& work) {
+        (void)redo; (void)work;
         const Side<float> SL = make_side(a.K, L), SR = make_side(a.K, R);
         const Star<float> s = riemann_star(a.K, SL, SR);
         if (near_vacuum_f32(L, R, s)) {
@@ -240,7 +243,14 @@ __device__ __forceinline__ int claim_tile(const SweepArgs<T>& a, int lane) {
             t = (i < a.ctr->redo_count[a.which]) ? a.redo_list[a.which * a.redo_cap + i] : -1;
         } else {
             const unsigned i = atomicAdd(&a.ctr->tile_ctr[a.which], 1u);
-            t = (i < (unsigned)a.ntiles) ? (int)i : -1;
+            if (a.ntiles_dev) {
+                // adaptive y tiles: long jobs from the front, then short ones
+                // from the back of the list
+                const unsigned nf = a.ntiles_dev[0], nb = a.ntiles_dev[1];
+                t = (i < nf) ? (int)i : (i < nf + nb) ? a.ntiles - 1 - (int)(i - nf) : -1;
+            } else {
+                t = (i < (unsigned)a.ntiles) ? (int)i : -1;
+            }
         }
     }
     return __shfl_sync(0xffffffffu, t, 0);
@@ -353,16 +363,28 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
 
     const Consts<T>& K = a.K;
     const unsigned acc = a.ctr->acc;
+    // FP64: every tile records its estimated work for the adaptive y tiles
+    constexpr bool kRecord = (VAR == VAR_F64);
     unsigned kbad = 0, nfb = 0;
     bool aborted = false;
 
     for (;;) {
         const int t = claim_tile<T, VAR>(a, lane);
         if (t < 0) break;
+        unsigned tcost = 0;  // estimated work of the tile (solve_work units)
         const Tile tile = a.tiles[t];
+        if (tile.grid < 0 || tile.grid >= a.ngrids) {
+            kbad |= STATUS_BAD_TILE;
+            continue;
+        }
         const GridDesc g = a.grids[tile.grid];
         const double dt = a.run[tile.grid].dt;
         const int n = g.ny, nlines = g.nx;
+        if (tile.cell0 < 0 || tile.ncell < 1 || tile.cell0 + tile.ncell > n || tile.line0 < 0 ||
+            tile.line0 >= nlines || (tile.line0 & (kWarpLines - 1))) {
+            kbad |= STATUS_BAD_TILE;  // never produced by the host or the tiler
+            continue;
+        }
         const int line0 = tile.line0, line = line0 + lane;
         const bool valid = line < nlines;
         const int lsafe = valid ? line : nlines - 1;
@@ -424,7 +446,10 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                 // at k = s0 the face left of cell s0-1 is not formed: solve a
                 // trivial problem (equal states) whose flux is never used
                 if (k == s0) w.wr0 = wl1;
-                const Cons<T> fhi = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb);
+                unsigned wk = 0;
+                const Cons<T> fhi = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb, wk);
+                // the warp's work at this row is that of its slowest lane
+                if (kRecord) tcost += __reduce_max_sync(0xffffffffu, wk);
                 if (k >= s0 + 2) {
                     const Cons<T> out = update(w.u0, dtdx, fhi, w.flo);
                     if (valid) {
@@ -451,6 +476,20 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
             }
         }
         if (aborted) break;
+        if (kRecord && a.ycost && lane == 0) {
+            // the tile's work, spread evenly over its cost blocks (the tile
+            // and grid fields are read again here rather than kept in
+            // registers through the walk)
+            const int4 tt = __ldcg(reinterpret_cast<const int4*>(a.tiles + t));  // grid, line0, cell0, ncell
+            const long long yblk = __ldcg(&a.grids[tt.x].yblk);
+            const int nrb = __ldcg(&a.grids[tt.x].nrb);
+            const int b0 = tt.z / kYBlock, b1 = (tt.z + tt.w - 1) / kYBlock;
+            const float dens = (float)tcost / (float)(b1 - b0 + 1);
+            float* cst = a.ycost + yblk + (long long)(tt.y / kWarpLines) * nrb;
+            for (int b = b0; b <= b1; ++b) cst[b] = dens;
+            const unsigned par = (unsigned)(__ldcg(&a.ctr->steps) & 1ull);
+            atomicAdd(&a.ctr->ycost_total[par], (unsigned long long)tcost);
+        }
         finish_tile<T, VAR, WHICH>(a, t, tile.grid, acc, redo && valid, tbad, smax, kbad, lane);
     }
 
@@ -633,8 +672,9 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
             Prim<T> WRm = shfl_up1(WRB);  // right face of A-1
             if (lane == 0) WRm = WLA;
             bool r1 = false, r2 = false;
-            const Cons<T> Fm = FluxOp<T, VAR>::eval(a, WRm, WLA, r1, nfb);  // A - 1/2
-            const Cons<T> Fc = FluxOp<T, VAR>::eval(a, WRA, WLB, r2, nfb);  // A + 1/2
+            unsigned wk = 0;  // scheduling work estimate, unused in x
+            const Cons<T> Fm = FluxOp<T, VAR>::eval(a, WRm, WLA, r1, nfb, wk);  // A - 1/2
+            const Cons<T> Fc = FluxOp<T, VAR>::eval(a, WRA, WLB, r2, nfb, wk);  // A + 1/2
             const Cons<T> Fp = shfl_down1(Fm);                              // B + 1/2
             const Cons<T> nA = update(uA, dtdx, Fc, Fm);
             const Cons<T> nB = update(uB, dtdx, Fp, Fc);

@@ -136,6 +136,19 @@ def test_results_identical_for_every_tile_shape_schedule_and_graph(precision):
         assert np.array_equal(got, ref), (tl, cps, gs, sl)
 
 
+def test_adaptive_y_tiles_match_static_tiles_on_a_growing_blast():
+    """FP64 y tiles are re-cut every step from the recorded cost of the
+    previous y sweep; on a blast the cost varies strongly across the grid.
+    Whatever the cut, the results equal those of fixed tilings bit for bit."""
+    pb = pr.sedov(200, 179)
+    ada, _, _ = gpu_run(pb, 60, precision=64,
+                        tuning=dict(tile_len=0, ctas_per_sm=0, graph_steps=20, span_len=0), record=False)
+    for tl in (8, 36, 256):
+        got, _, _ = gpu_run(pb, 60, precision=64,
+                            tuning=dict(tile_len=tl, ctas_per_sm=0, graph_steps=0, span_len=0), record=False)
+        assert np.array_equal(got, ada), tl
+
+
 def _vacuum_pair(n=64, ny=6):
     """Two streams leaving each other: a strong double rarefaction whose
     interfaces need the FP64 solve in the FP32 path."""
