@@ -256,12 +256,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if sampler:
         sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.stats()["kernel_launches"]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     e0.record(stream)
     ctx.step(args.steps)
     e1.record(stream)
+    launches = ctx.stats()["kernel_launches"] - launches0
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -381,7 +383,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": launches,
         "clocks": clocks,
         "kernels_ms": {"prologue": prologue_ms, "sweep": sweep_ms, "x_sweep": x_ms, "y_sweep": y_ms},
         "riemann_fp64_fallbacks": stats["riemann_fp64"],

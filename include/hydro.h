@@ -119,11 +119,15 @@ typedef struct {
  *   status_flags   bit 0: non-positive/NaN density, bit 1: non-positive/NaN
  *                  energy, bit 2: a bounded wait timed out, bit 3: internal
  *                  error, a tile outside its grid was skipped (sticky until
- *                  hydro_set_state) */
+ *                  hydro_set_state)
+ *   kernel_launches  kernels the step calls launched (host count; a step of
+ *                  an FP64 context launches 6 with adaptive y tiles, of an
+ *                  FP32 context 5) */
 typedef struct {
     long long steps;
     long long riemann_fp64;
     unsigned int status_flags;
+    long long kernel_launches;
 } hydro_stats;
 
 /* Create a context: validates params, allocates two state buffers (the step

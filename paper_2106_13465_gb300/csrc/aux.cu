@@ -19,6 +19,7 @@ __global__ void step_prologue_kernel(GridRun* run, const GridDesc* grids, int ng
         run[g].dt = dt;
         run[g].t += dt;
         run[g].wmax[dst] = 0ull;
+        run[g].smax32 = 0u;
         if (dt_log) dt_log[g] = dt;
     }
     __syncthreads();

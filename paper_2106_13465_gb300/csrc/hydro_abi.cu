@@ -94,6 +94,8 @@ struct hydro_ctx {
     int* d_redo = nullptr;          // [2][redo_cap] FP32 second-pass tile lists
     float* d_ycost = nullptr;       // recorded y-sweep cost per block (adaptive y tiles)
     Tile* d_ystat = nullptr;        // static y tiling the adaptive tiles split
+    Strip* d_strips = nullptr;      // row strips of the FP64 CFL passes
+    int nstrips = 0;
     int nystat = 0;
     long long nyblocks = 0;         // cost blocks of all grids
     bool y_adaptive = false;        // y tiles cut from recorded costs every step
@@ -104,6 +106,7 @@ struct hydro_ctx {
     int ctas[2] = {0, 0};       // CTAs per sweep launch (x, y)
     int tile_len_used[2] = {0, 0};
     long long step = 0;         // steps since the last hydro_set_state
+    long long launches = 0;     // kernels launched by the step calls since hydro_init
     cudaGraphExec_t gexec = nullptr;
     int gexec_steps = 0;
     std::string err;
@@ -411,6 +414,10 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
         if (dir == DIR_Y && c->y_adaptive) a.ntiles_dev = c->d_ctr->ytiles;
         if (sizeof(T) == 8) {
             e = launch_sweep<T>(dir, VAR_F64, a, c->ctas[dir], s);
+            // the second sweep's new state: its max wave speed (next dt)
+            if (e == cudaSuccess && which == 1)
+                e = launch_cfl_fp64((const double*)c->buf[0], c->d_grids, c->d_strips, c->nstrips, c->d_run,
+                                    c->d_ctr, c->Kd, c->nsm * 8, s);
         } else {
             // main FP32 pass, then the second pass over tiles it queued
             e = launch_sweep<T>(dir, VAR_F32_MAIN, a, c->ctas[dir], s);
@@ -420,6 +427,13 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
         if (ev && (e = cudaEventRecord(ev[2 + which], s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Kernels one step launches (enqueue_step_t): the dt prologue, the y tiler
+// (adaptive y tiles), and per sweep the sweep kernel plus, FP64, the two CFL
+// passes after the second sweep or, FP32, the near-vacuum second pass.
+int launches_per_step(const hydro_ctx* c) {
+    return 1 + (c->y_adaptive ? 1 : 0) + (c->prec == 64 ? 2 + 2 : 2 * 2);
 }
 
 cudaError_t enqueue_step(hydro_ctx* c, int parity, const double* ovr, double* log, cudaStream_t s,
@@ -562,6 +576,19 @@ hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
         (st = alloc((void**)&c->d_stage, sizeof(double) * 4 * max_cells, "staging")) != HYDRO_OK)
         return bail(st);
     if ((st = alloc((void**)&c->d_ycost, sizeof(float) * c->nyblocks, "y cost blocks")) != HYDRO_OK) return bail(st);
+    {
+        // the FP64 CFL passes walk the grids in strips of whole rows, ~8192 cells each
+        std::vector<Strip> strips;
+        for (int g = 0; g < (int)c->gd.size(); ++g) {
+            const GridDesc& d = c->gd[g];
+            const int rows = std::max(1, std::min(d.ny, 8192 / d.nx));
+            for (int r = 0; r < d.ny; r += rows) strips.push_back(Strip{g, r, std::min(rows, d.ny - r), 0});
+        }
+        c->nstrips = (int)strips.size();
+        if ((st = alloc((void**)&c->d_strips, sizeof(Strip) * strips.size(), "cfl strips")) != HYDRO_OK) return bail(st);
+        e = cudaMemcpy(c->d_strips, strips.data(), sizeof(Strip) * strips.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { fail_cuda(c, "cfl strips upload", e); return bail(HYDRO_ECUDA); }
+    }
 
     e = cudaMemcpy(c->d_grids, c->gd.data(), sizeof(GridDesc) * c->gd.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_run, 0, sizeof(GridRun) * c->gd.size());
@@ -595,6 +622,7 @@ void hydro_destroy(hydro_ctx* c) {
     cudaFree(c->d_redo);
     cudaFree(c->d_ycost);
     cudaFree(c->d_ystat);
+    cudaFree(c->d_strips);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -712,6 +740,7 @@ hydro_status hydro_step_dt(hydro_ctx* c, int nsteps, const double* dt_override, 
         HCK(c, enqueue_step(c, (int)(c->step & 1), ovr, log, c->stream));
         ++c->step;
     }
+    c->launches += (long long)nsteps * launches_per_step(c);
     unsigned int status = 0;
     HCK(c, cudaMemcpyAsync(&status, &c->d_ctr->status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
     if (dt_used)
@@ -735,7 +764,10 @@ hydro_status hydro_step_profiled(hydro_ctx* c, int nsteps, double* kernel_ms) {
     for (int s = 0; s < nsteps && st == HYDRO_OK; ++s) {
         cudaError_t e = enqueue_step(c, (int)(c->step & 1), nullptr, nullptr, c->stream, &ev[4 * (size_t)s]);
         if (e != cudaSuccess) st = fail_cuda(c, "profiled step", e);
-        else ++c->step;
+        else {
+            ++c->step;
+            c->launches += launches_per_step(c);
+        }
     }
     if (st == HYDRO_OK) {
         cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -822,6 +854,7 @@ hydro_status hydro_get_stats(hydro_ctx* c, hydro_stats* out) {
     out->steps = (long long)ctr.steps;
     out->riemann_fp64 = (long long)ctr.riemann_fp64;
     out->status_flags = ctr.status;
+    out->kernel_launches = c->launches;
     return HYDRO_OK;
 }
 

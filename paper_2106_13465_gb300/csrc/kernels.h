@@ -95,6 +95,13 @@ struct GridRun {
     double t;                    // simulated time
     unsigned long long wmax[2];  // max wave speed (bits of a double >= 0) of the
                                  // state, double-buffered by step parity
+    unsigned int smax32;         // FP64 contexts: max FP32 estimate of the wave
+                                 // speed of the step's new state (bits of a float)
+};
+
+// A run of whole rows of one grid (the CFL passes of FP64 contexts).
+struct Strip {
+    int grid, row0, nrows, pad;
 };
 
 // Context-wide device counters.
@@ -140,6 +147,17 @@ template <class T>
 int sweep_ctas_per_sm(int dir, int var);
 
 // ---- launchers (defined in the kernel translation units) ------------------
+// FP64 contexts: the max wave speed of the state a step produced, in two
+// passes over the strips: an FP32 estimate of every cell's speed and its
+// per-grid max M, then the exact FP64 speed of every cell whose estimate is
+// not below M (1 - kCflScreen) (all cells if M is not finite), folded into
+// wmax[acc].  The estimate is within kCflScreen / 2 of the exact speed, so
+// the cell of the exact maximum is always among those evaluated in FP64.
+constexpr float kCflScreen = 1e-3f;
+cudaError_t launch_cfl_fp64(const double* state, const GridDesc* grids, const Strip* strips, int nstrips,
+                            GridRun* run, const DevCounters* ctr, const Consts<double>& K, int nctas,
+                            cudaStream_t s);
+
 template <class T>
 cudaError_t launch_sweep(int dir, int var, const SweepArgs<T>& a, int nctas, cudaStream_t s);
 

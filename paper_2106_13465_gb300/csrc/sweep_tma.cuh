@@ -270,7 +270,7 @@ __device__ __forceinline__ void finish_tile(const SweepArgs<T>& a, int t, int gr
         return;
     }
     kbad |= tbad;
-    if (WHICH == 1) {
+    if (WHICH == 1 && sizeof(T) == 4) {
         double m = (double)smax;
         for (int o = 16; o > 0; o >>= 1) {
             const double v = __shfl_xor_sync(0xffffffffu, m, o);
@@ -285,7 +285,10 @@ template <class T, int WHICH>
 __device__ __forceinline__ void check_cell(const Consts<T>& K, const Cons<T>& out, unsigned& tbad, T& smax) {
     tbad |= positive(out.r) ? 0u : STATUS_BAD_RHO;
     tbad |= positive(out.E) ? 0u : STATUS_BAD_E;
-    if (WHICH == 1) {
+    // FP32: the CFL wave speed of the new state (next step's dt) is folded
+    // in here; FP64 forms it after the sweep (launch_cfl_fp64), where only
+    // the few cells near the maximum pay for the FP64 speed
+    if (WHICH == 1 && sizeof(T) == 4) {
         const T sp = cfl_speed(K, out);
         smax = (sp <= smax) ? smax : sp;
     }

@@ -51,7 +51,7 @@ class hydro_tuning(ctypes.Structure):
 
 class hydro_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("riemann_fp64", ctypes.c_longlong),
-                ("status_flags", ctypes.c_uint)]
+                ("status_flags", ctypes.c_uint), ("kernel_launches", ctypes.c_longlong)]
 
 
 _lib = None
@@ -322,4 +322,5 @@ class Context:
     def stats(self) -> dict:
         st, s = hydro_get_stats(self.ctx)
         self._check(st)
-        return {"steps": s.steps, "riemann_fp64": s.riemann_fp64, "status_flags": s.status_flags}
+        return {"steps": s.steps, "riemann_fp64": s.riemann_fp64, "status_flags": s.status_flags,
+                "kernel_launches": s.kernel_launches}

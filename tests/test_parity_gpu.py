@@ -149,6 +149,21 @@ def test_adaptive_y_tiles_match_static_tiles_on_a_growing_blast():
         assert np.array_equal(got, ada), tl
 
 
+@pytest.mark.parametrize("precision,per_step", [(64, 6), (32, 5)])
+def test_kernel_launch_count_reported(precision, per_step):
+    """hydro_stats counts the kernels the step calls launch (bench.py reports
+    it as gpu_launches): FP64 prologue, y tiler, two sweeps, two CFL passes;
+    FP32 prologue and two sweeps of two passes each."""
+    pb = pr.sedov(64, 48)
+    with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=precision) as c:
+        c.set_state(0, pb.U)
+        n0 = c.stats()["kernel_launches"]
+        c.step(3)
+        c.step(40)
+        c.step_profiled(2)
+        assert c.stats()["kernel_launches"] - n0 == 45 * per_step
+
+
 def _vacuum_pair(n=64, ny=6):
     """Two streams leaving each other: a strong double rarefaction whose
     interfaces need the FP64 solve in the FP32 path."""
