@@ -121,7 +121,7 @@ typedef struct {
  *                  error, a tile outside its grid was skipped (sticky until
  *                  hydro_set_state)
  *   kernel_launches  kernels the step calls launched (host count; a step of
- *                  an FP64 context launches 6 with adaptive y tiles, of an
+ *                  an FP64 context launches 5 with adaptive y tiles, of an
  *                  FP32 context 5) */
 typedef struct {
     long long steps;

@@ -430,10 +430,10 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
 }
 
 // Kernels one step launches (enqueue_step_t): the dt prologue, the y tiler
-// (adaptive y tiles), and per sweep the sweep kernel plus, FP64, the two CFL
-// passes after the second sweep or, FP32, the near-vacuum second pass.
+// (adaptive y tiles), and per sweep the sweep kernel plus, FP64, the CFL
+// pass after the second sweep or, FP32, the near-vacuum second pass.
 int launches_per_step(const hydro_ctx* c) {
-    return 1 + (c->y_adaptive ? 1 : 0) + (c->prec == 64 ? 2 + 2 : 2 * 2);
+    return 1 + (c->y_adaptive ? 1 : 0) + (c->prec == 64 ? 2 + 1 : 2 * 2);
 }
 
 cudaError_t enqueue_step(hydro_ctx* c, int parity, const double* ovr, double* log, cudaStream_t s,

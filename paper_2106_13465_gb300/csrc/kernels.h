@@ -147,13 +147,14 @@ template <class T>
 int sweep_ctas_per_sm(int dir, int var);
 
 // ---- launchers (defined in the kernel translation units) ------------------
-// FP64 contexts: the max wave speed of the state a step produced, in two
-// passes over the strips: an FP32 estimate of every cell's speed and its
-// per-grid max M, then the exact FP64 speed of every cell whose estimate is
-// not below M (1 - kCflScreen) (all cells if M is not finite), folded into
-// wmax[acc].  The estimate is within kCflScreen / 2 of the exact speed, so
-// the cell of the exact maximum is always among those evaluated in FP64.
-constexpr float kCflScreen = 1e-3f;
+// FP64 contexts: the max wave speed of the state a step produced.  The
+// second sweep keeps the per-grid max M of an FP32 estimate of every new
+// cell's speed (smax32); this pass over the strips then evaluates the exact
+// FP64 speed of every cell whose estimate is not below M (1 - kCflScreen)
+// (all cells if M is not finite) and folds it into wmax[acc].  The estimate
+// is within 2e-3 of the exact speed (relative), well inside kCflScreen / 2,
+// so the cell of the exact maximum is always among those evaluated in FP64.
+constexpr float kCflScreen = 1e-2f;
 cudaError_t launch_cfl_fp64(const double* state, const GridDesc* grids, const Strip* strips, int nstrips,
                             GridRun* run, const DevCounters* ctr, const Consts<double>& K, int nctas,
                             cudaStream_t s);

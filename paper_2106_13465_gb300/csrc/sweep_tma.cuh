@@ -232,6 +232,42 @@ struct WarpRing {
     }
 };
 
+// ---- FP32 estimate of the CFL wave speed of an FP64 state ------------------
+// FP64 -> FP32 by truncating the significand on the integer pipe (the FP64
+// pipe, the sweep's bottleneck, stays free): relative error below 2^-23 for
+// values in the FP32 normal range, +-0 below it, +-inf above it and for NaN.
+__device__ __forceinline__ float f32_trunc(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+    if (e <= 0) return __uint_as_float(sign);
+    return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
+// FP32 estimate of cfl_speed of an FP64 state, used to find the few cells
+// that need the exact FP64 speed.  Its relative error is below 2e-3 for every
+// state whose values are finite in FP32: the inputs and the FP32 operations
+// round to a few 1e-7, except where the pressure comes from cancellation
+// (kinetic energy far above the internal energy); there the absolute error
+// of c is at most sqrt(g (g - 1) k eps32) |u| (k ~ 5 roundings), under 1e-3
+// of the speed, which the flow speed then dominates.  An infinite or NaN
+// estimate (overflow, NaN input) sends every cell of the grid to the exact
+// evaluation.
+__device__ __forceinline__ float cfl_estimate(const Consts<double>& K, double r, double mn, double mt, double E) {
+    const float rfl = (float)K.rho_floor, gm1 = (float)K.gm1, gam = (float)K.gamma, cf2g = (float)K.cf2g;
+    float rho = f32_trunc(r);
+    rho = (rho < rfl) ? rfl : rho;
+    const float ir = 1.0f / rho;
+    const float u = f32_trunc(mn) * ir, v = f32_trunc(mt) * ir;
+    float p = gm1 * (f32_trunc(E) - 0.5f * rho * (u * u + v * v));
+    const float pm = rho * cf2g;
+    p = (p < pm) ? pm : p;
+    const float c = sqrtf(gam * p * ir);
+    return fmaxf(fabsf(u), fabsf(v)) + c;
+}
+
 // Claim the next tile: the main pass takes the work list in order, the FP32
 // second pass takes the tiles the main pass queued.  -1 when none is left.
 template <class T, int VAR>
@@ -261,7 +297,7 @@ __device__ __forceinline__ int claim_tile(const SweepArgs<T>& a, int lane) {
 // bits and, on the second sweep of a step, its wave-speed maximum are kept.
 template <class T, int VAR, int WHICH>
 __device__ __forceinline__ void finish_tile(const SweepArgs<T>& a, int t, int grid, unsigned acc, bool redo,
-                                            unsigned tbad, T smax, unsigned& kbad, int lane) {
+                                            unsigned tbad, T smax, unsigned sbits, unsigned& kbad, int lane) {
     if (VAR == VAR_F32_MAIN && __any_sync(0xffffffffu, redo)) {
         if (lane == 0) {
             const unsigned i = atomicAdd(&a.ctr->redo_count[a.which], 1u);
@@ -270,6 +306,11 @@ __device__ __forceinline__ void finish_tile(const SweepArgs<T>& a, int t, int gr
         return;
     }
     kbad |= tbad;
+    if (WHICH == 1 && sizeof(T) == 8) {
+        // FP64: max of the FP32 speed estimates (bits order as unsigned)
+        const unsigned m = __reduce_max_sync(0xffffffffu, sbits);
+        if (lane == 0 && m) atomicMax(&a.run[grid].smax32, m);
+    }
     if (WHICH == 1 && sizeof(T) == 4) {
         double m = (double)smax;
         for (int o = 16; o > 0; o >>= 1) {
@@ -282,13 +323,19 @@ __device__ __forceinline__ void finish_tile(const SweepArgs<T>& a, int t, int gr
 
 // Status bits and (second sweep) CFL wave speed of one new cell state.
 template <class T, int WHICH>
-__device__ __forceinline__ void check_cell(const Consts<T>& K, const Cons<T>& out, unsigned& tbad, T& smax) {
+__device__ __forceinline__ void check_cell(const Consts<T>& K, const Cons<T>& out, unsigned& tbad, T& smax,
+                                           unsigned& sbits) {
     tbad |= positive(out.r) ? 0u : STATUS_BAD_RHO;
     tbad |= positive(out.E) ? 0u : STATUS_BAD_E;
     // FP32: the CFL wave speed of the new state (next step's dt) is folded
-    // in here; FP64 forms it after the sweep (launch_cfl_fp64), where only
-    // the few cells near the maximum pay for the FP64 speed
-    if (WHICH == 1 && sizeof(T) == 4) {
+    // in here.  FP64: only an FP32 estimate here; after the sweep the cells
+    // whose estimate is near the grid's maximum get the exact FP64 speed
+    // (launch_cfl_fp64), so the FP64 pipe works on a few cells only
+    if constexpr (WHICH == 1 && sizeof(T) == 8) {
+        const unsigned b = __float_as_uint(cfl_estimate(K, out.r, out.mn, out.mt, out.E));
+        sbits = (b > sbits) ? b : sbits;
+    }
+    if constexpr (WHICH == 1 && sizeof(T) == 4) {
         const T sp = cfl_speed(K, out);
         smax = (sp <= smax) ? smax : sp;
     }
@@ -411,6 +458,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
         YWalk<T> w = {};
         Cons<T> gsave = {};  // mirror of row n-2, kept for position n+1
         T smax = T(0);
+        unsigned sbits = 0;  // FP64: max FP32 speed estimate (float bits)
         unsigned tbad = 0;
         bool redo = false;
 
@@ -461,7 +509,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                         qn[o] = out.mn;
                         qt[o] = out.mt;
                         qe[o] = out.E;
-                        check_cell<T, WHICH>(K, out, tbad, smax);
+                        check_cell<T, WHICH>(K, out, tbad, smax, sbits);
                     }
                 }
                 w.flo = fhi;
@@ -493,7 +541,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
             const unsigned par = (unsigned)(__ldcg(&a.ctr->steps) & 1ull);
             atomicAdd(&a.ctr->ycost_total[par], (unsigned long long)tcost);
         }
-        finish_tile<T, VAR, WHICH>(a, t, tile.grid, acc, redo && valid, tbad, smax, kbad, lane);
+        finish_tile<T, VAR, WHICH>(a, t, tile.grid, acc, redo && valid, tbad, smax, sbits, kbad, lane);
     }
 
     if (aborted && lane == 0) {
@@ -613,6 +661,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
         const T hdtdx = T(-0.5) * dtdx;
         T* __restrict__ drow = a.dst + g.off + (long long)row * g.pitch;
         T smax = T(0);
+        unsigned sbits = 0;  // FP64: max FP32 speed estimate (float bits)
         unsigned tbad = 0;
         bool redo = false;
 
@@ -687,8 +736,8 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
             redo |= (r1 || r2) && lo;
             if (lo) {
                 store_pair<T>(drow + A, g.plane, nA, nB, lo, hi);
-                check_cell<T, WHICH>(K, nA, tbad, smax);
-                if (hi) check_cell<T, WHICH>(K, nB, tbad, smax);
+                check_cell<T, WHICH>(K, nA, tbad, smax, sbits);
+                if (hi) check_cell<T, WHICH>(K, nB, tbad, smax, sbits);
             }
             // the flux at B+1/2 (from lane l+1) feeds B: ask for a second pass
             // there too when lane l+1 solved it in FP32 near vacuum
@@ -696,7 +745,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
             redo |= r1n && lo && hi;
         }
         if (aborted) break;
-        finish_tile<T, VAR, WHICH>(a, t, tile.grid, acc, redo, tbad, smax, kbad, lane);
+        finish_tile<T, VAR, WHICH>(a, t, tile.grid, acc, redo, tbad, smax, sbits, kbad, lane);
     }
 
     if (aborted && lane == 0) {

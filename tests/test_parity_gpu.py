@@ -149,10 +149,10 @@ def test_adaptive_y_tiles_match_static_tiles_on_a_growing_blast():
         assert np.array_equal(got, ada), tl
 
 
-@pytest.mark.parametrize("precision,per_step", [(64, 6), (32, 5)])
+@pytest.mark.parametrize("precision,per_step", [(64, 5), (32, 5)])
 def test_kernel_launch_count_reported(precision, per_step):
     """hydro_stats counts the kernels the step calls launch (bench.py reports
-    it as gpu_launches): FP64 prologue, y tiler, two sweeps, two CFL passes;
+    it as gpu_launches): FP64 prologue, y tiler, two sweeps, the CFL pass;
     FP32 prologue and two sweeps of two passes each."""
     pb = pr.sedov(64, 48)
     with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=precision) as c:
@@ -257,6 +257,34 @@ def test_dt_record_and_override_replay():
         assert c.cfl_dt(0) == pytest.approx(O.cfl_dt(pb.U, pb.h), rel=1e-14)
         c.step(12)
         assert c.time(0) == pytest.approx(float(np.sum(gdts)), rel=1e-14)
+
+
+@pytest.mark.parametrize("mach,drho", [(0.5, 1e-2), (1e3, 1e-4)])
+def test_cfl_max_found_exactly_after_fp32_screen(mach, drho):
+    """FP64 contexts find the max wave speed of a new state from an FP32
+    screen plus the exact FP64 speed of the cells near the screen's maximum.
+    dt must equal that of the oracle's exact maximum, also at Mach 1000 where
+    the FP32 pressure carries ~10 % cancellation error, and with every cell
+    within 1e-5 of the maximum (all near-ties)."""
+    rng = np.random.default_rng(11)
+    ny, nx = 40, 56
+    rho = 1.0 + drho * rng.standard_normal((ny, nx))
+    p = 1.0 / (1.4 * mach * mach)  # sound speed 1/mach, flow speed ~1
+    u = 1.0 + 1e-6 * rng.standard_normal((ny, nx))
+    v = 1e-3 * rng.standard_normal((ny, nx))
+    U = pr.conserved(rho, u, v, p)
+    pb = pr.Problem("mach", U, 1.0 / nx, (P_,) * 4)
+    want, odts, _ = O.run(pb.U, pb.h, pb.bc, 4)
+    got, gdts, _ = gpu_run(pb, 4)
+    assert np.allclose(gdts, odts, rtol=1e-13, atol=0)
+    # The transverse momentum here is ~1e-3 of the other variables but is
+    # updated by pressure-scale fluxes, so rounding is measured against the
+    # largest state variable.  At Mach M the pressure comes from cancellation
+    # (E - rho q^2 / 2), which amplifies rounding differences by ~M^2 eps /
+    # (gamma - 1): 1e-13 of the scale at M = 0.5, ~1e-10 at M = 1000.
+    scale = float(np.abs(want).max())
+    tol = 1e-13 if mach < 10 else 1e-9
+    assert float(np.abs(got - want).max()) <= tol * scale
 
 
 def test_conservation_sums_on_device():
