@@ -577,11 +577,11 @@ hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
         return bail(st);
     if ((st = alloc((void**)&c->d_ycost, sizeof(float) * c->nyblocks, "y cost blocks")) != HYDRO_OK) return bail(st);
     {
-        // the FP64 CFL passes walk the grids in strips of whole rows, ~8192 cells each
+        // the FP64 CFL pass walks the grids in strips of whole rows, ~2048 cells each
         std::vector<Strip> strips;
         for (int g = 0; g < (int)c->gd.size(); ++g) {
             const GridDesc& d = c->gd[g];
-            const int rows = std::max(1, std::min(d.ny, 8192 / d.nx));
+            const int rows = std::max(1, std::min(d.ny, 2048 / d.nx));
             for (int r = 0; r < d.ny; r += rows) strips.push_back(Strip{g, r, std::min(rows, d.ny - r), 0});
         }
         c->nstrips = (int)strips.size();
