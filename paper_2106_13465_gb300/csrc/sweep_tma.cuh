@@ -2,35 +2,35 @@
 // and WRITE steps of Fig. 5 fused into one pass over HBM), included by the
 // FP64 and FP32 translation units.
 //
-// Work decomposition.  A persistent grid of CTAs whose warps claim warp tiles
-// (32 lines x ncell cells of one grid) from a work counter, so one launch
-// covers any number of grids of any shapes.  Lane l owns line line0 + l and
-// walks it from cell cell0 - 2 to cell0 + ncell + 1 (the 5-point stencil of
-// Figs. 1-2), keeping a 2-cell window of conserved and primitive states, the
-// right face of the previous cell and the flux at the previous interface in
-// registers: every interface is solved once, every cell is written once.
+// Work decomposition.  A persistent grid of CTAs whose warps claim tasks from
+// a work counter, so one launch covers any number of grids of any shapes.
+//   x sweep: a task is a run of overlapping 64-cell segments of one row
+//            (segment k starts at x = -4 + 60 k); lane l holds cells 2l and
+//            2l+1 of the segment and takes its neighbours' primitives, faces
+//            and fluxes by warp shuffles; lanes 1..30 hold the 60 results.
+//   y sweep: a task (tile) is 32 columns x L rows; lane l walks column
+//            line0 + l from row cell0 - 2 to cell0 + L + 1 (the 5-point
+//            stencil of Figs. 1-2) with a 2-cell window of conserved and
+//            primitive states, the right face of the previous cell and the
+//            flux at the previous interface in registers.
+// In both, every interface is solved once per task and every cell written
+// once.
 //
 // Data movement.  Each warp owns a ring of shared-memory slots fed by TMA
 // (cp.async.bulk.tensor, one elected lane, completion on an mbarrier per
-// slot).  A slot holds one chunk: 32 lines x C cells x 4 planes.
-//   x sweep: lines are rows; a chunk is 32 rows x 16 bytes of x per plane
-//            (C = 4 FP32 / 2 FP64 cells), 16-byte rows in shared memory, so
-//            lane r reads its cells with one 16-byte load per plane (rows r,
-//            r+8, r+16, r+24 share banks: 4 wavefronts per 512 bytes, the
-//            minimum).  Results are written back in place and the chunk is
-//            stored with a TMA tile store: reads and writes both coalesced
-//            with no global transpose.
-//   y sweep: lines are columns; a chunk is 4 rows x 32 columns per plane;
-//            lane l reads column l (consecutive words), and writes its results
-//            straight to global memory (a warp writes 32 consecutive cells).
-// The ring is refilled as chunks are consumed, so several chunks per warp are
-// in flight while the warp computes.
+// slot).  x: a slot holds one segment (64 cells x 4 planes); lane l reads its
+// two cells with one 8- or 16-byte load per plane, and the warp writes its 60
+// results as consecutive cells of each plane.  y: a slot holds 4 rows x 32
+// columns x 4 planes; lane l reads column l (consecutive words) and a warp
+// writes 32 consecutive cells per plane.  The ring is refilled as slots are
+// consumed, so several are in flight while the warp computes.
 //
 // Boundary conditions are folded into the read: a position k outside [0, n)
 // of a line takes the mirror cell (reflective: normal momentum negated;
-// transmissive) or the wrap-around cell (periodic).  Mirror cells are read
-// from the ring or from the register window; wrap-around cells with a direct
-// load.  TMA reads outside the grid are zero-filled and never used.
+// transmissive) or the wrap-around cell (periodic).  Mirror cells come by
+// shuffle from the same x segment, or from the first y chunk and the y
+// walker's register window; wrap-around cells with a direct load.  TMA reads
+// outside the grid are zero-filled and feed no result.
 //
 // Every wait on an mbarrier is bounded: after kWaitLimit polls the warp
 // records STATUS_TIMEOUT, waits (bounded again) for its own copies still in
