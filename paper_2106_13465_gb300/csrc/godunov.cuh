@@ -142,6 +142,17 @@ __device__ __forceinline__ float minmod(float a, float b) {
     return (a * b > 0.0f) ? ((fabsf(a) < fabsf(b)) ? a : b) : 0.0f;
 }
 
+// Bitwise equality of two primitive states (integer pipe; +0 and -0 differ,
+// which only sends such a pair down the general path).
+__device__ __forceinline__ bool same_bits(double a, double b) {
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_int(a) == __float_as_int(b); }
+template <class T>
+__device__ __forceinline__ bool same_bits(const Prim<T>& a, const Prim<T>& b) {
+    return same_bits(a.r, b.r) && same_bits(a.u, b.u) && same_bits(a.v, b.v) && same_bits(a.p, b.p);
+}
+
 // x > 0 for x not NaN (positive finite or +inf), tested on the bit pattern.
 __device__ __forceinline__ bool positive(double x) {
     const long long i = __double_as_longlong(x);
@@ -158,10 +169,19 @@ __device__ __forceinline__ bool positive(float x) {
 //   rho: u D_rho + rho D_u,  u_n: u D_u + D_p/rho,  u_t: u D_ut,
 //   p: g p D_u + u D_p;
 // faces WL = W0 - D/2 + dW (left), WR = W0 + D/2 + dW (right), floored.
+//
+// Between two neighbours equal to it (bit for bit) every slope is 0, the
+// predictor is -0 and each face equals W0 exactly (W0 is already floored):
+// that case returns W0 without the arithmetic.
 template <class T>
 __device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) */,
                                       const Prim<T>& Wm, const Prim<T>& W0, T ir0 /* 1/rho_0 */,
                                       const Prim<T>& Wp, Prim<T>& WL, Prim<T>& WR) {
+    if (same_bits(Wm, W0) && same_bits(Wp, W0)) {
+        WL = W0;
+        WR = W0;
+        return;
+    }
     const T Dr = minmod(W0.r - Wm.r, Wp.r - W0.r);
     const T Du = minmod(W0.u - Wm.u, Wp.u - W0.u);
     const T Dv = minmod(W0.v - Wm.v, Wp.v - W0.v);
@@ -383,16 +403,30 @@ __device__ __forceinline__ T sound_speed(const Consts<T>& K, const Prim<T>& W) {
     return tsqrt(K.gamma * W.p / W.r);
 }
 
-// A rough count of the FP64 operations of one interface solve, used only to
-// schedule work (adaptive y tiles): a fixed part (sides, guess, sampling,
-// flux), and per evaluation of the pressure functions the Newton update and
-// both sides, where a rarefaction power far from p_K (exp2/log2) costs about
-// four times the series near it.
+// Work of a cell whose interface has equal states (solve_work units): its
+// conversion, update and physical flux.
+constexpr unsigned kEqualStateWork = 40u;
+
+// A rough count of the FP64 operations of a cell and its interface solve,
+// used only to schedule work (adaptive y tiles): a fixed part (conversion,
+// trace, update, sides, guess, sampling, flux), and per evaluation of the
+// pressure functions the Newton update and both sides, where a rarefaction
+// power far from p_K (exp2/log2) costs about four times the series near it.
 template <class T>
 __device__ __forceinline__ unsigned solve_work(const Consts<T>& K, const Star<T>& s) {
     const unsigned pl = (s.pzl > T(0) && s.pzl < K.pz_series) ? 40u : 0u;
     const unsigned pr = (s.pzr > T(0) && s.pzr < K.pz_series) ? 40u : 0u;
-    return 100u + (unsigned)s.iters * (40u + pl + pr);
+    return 140u + (unsigned)s.iters * (40u + pl + pr);
+}
+
+// Equal states (bit for bit): the Riemann problem's solution is that state
+// everywhere, so the flux is its physical flux.  The general path gives the
+// same bits: p* = p and f_K = 0 exactly, u* = (u + u)/2 (which turns -0 into
+// +0, reproduced here), and the sampling returns the state.
+template <class T>
+__device__ __forceinline__ Cons<T> equal_state_flux(const Consts<T>& K, Prim<T> W) {
+    if (same_bits(W.u, -T(0))) W.u = T(0);
+    return physical_flux(K, W);
 }
 
 // Godunov flux at one interface between the traced states L | R.
@@ -400,6 +434,11 @@ template <class T>
 __device__ __forceinline__ Cons<T> godunov_flux_exact(const Consts<T>& K, const Prim<T>& WL,
                                                       const Prim<T>& WR, bool* floored,
                                                       unsigned* work = nullptr) {
+    if (same_bits(WL, WR)) {
+        if (floored) *floored = false;
+        if (work) *work = kEqualStateWork;
+        return equal_state_flux(K, WL);
+    }
     const Side<T> L = make_side(K, WL), R = make_side(K, WR);
     const Star<T> s = riemann_star(K, L, R);
     if (floored) *floored = s.floored;

@@ -130,6 +130,7 @@ struct FluxOp<float, VAR_F32_MAIN> {
                                                        const Prim<float>& R, bool& redo, unsigned& nfb,
                                                        unsigned& work) {
         (void)nfb; (void)work;
+        if (same_bits(L, R)) return equal_state_flux(a.K, L);  // equal states: no solve, no FP64
         const Side<float> SL = make_side(a.K, L), SR = make_side(a.K, R);
         const Star<float> s = riemann_star(a.K, SL, SR);
         if (near_vacuum_f32(L, R, s)) redo = true;
@@ -148,6 +149,7 @@ struct FluxOp<float, VAR_F32_REDO> {
                                                        const Prim<float>& R, bool& redo, unsigned& nfb,
                                                        unsigned& work) {
         (void)redo; (void)work;
+        if (same_bits(L, R)) return equal_state_flux(a.K, L);
         const Side<float> SL = make_side(a.K, L), SR = make_side(a.K, R);
         const Star<float> s = riemann_star(a.K, SL, SR);
         if (near_vacuum_f32(L, R, s)) {
