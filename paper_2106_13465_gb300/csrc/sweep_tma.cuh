@@ -130,7 +130,7 @@ struct FluxOp<float, VAR_F32_MAIN> {
                                                        const Prim<float>& R, bool& redo, unsigned& nfb,
                                                        unsigned& work) {
         (void)nfb; (void)work;
-        if (same_bits(L, R)) return equal_state_flux(a.K, L);  // equal states: no solve, no FP64
+        if (Shortcuts<float>::flux && same_bits(L, R)) return equal_state_flux(a.K, L);  // no solve, no FP64
         const Side<float> SL = make_side(a.K, L), SR = make_side(a.K, R);
         const Star<float> s = riemann_star(a.K, SL, SR);
         if (near_vacuum_f32(L, R, s)) redo = true;
@@ -149,7 +149,7 @@ struct FluxOp<float, VAR_F32_REDO> {
                                                        const Prim<float>& R, bool& redo, unsigned& nfb,
                                                        unsigned& work) {
         (void)redo; (void)work;
-        if (same_bits(L, R)) return equal_state_flux(a.K, L);
+        if (Shortcuts<float>::flux && same_bits(L, R)) return equal_state_flux(a.K, L);
         const Side<float> SL = make_side(a.K, L), SR = make_side(a.K, R);
         const Star<float> s = riemann_star(a.K, SL, SR);
         if (near_vacuum_f32(L, R, s)) {
@@ -323,6 +323,20 @@ __device__ __forceinline__ void finish_tile(const SweepArgs<T>& a, int t, int gr
     }
 }
 
+// Work (solve_work units) of a row whose 5-point stencil is uniform: no
+// arithmetic at all, the cell is copied.
+constexpr unsigned kUniformWork = 4u;
+
+// Bitwise equality of two conserved states.
+template <class T>
+__device__ __forceinline__ auto diff_bits(const Cons<T>& a, const Cons<T>& b) {
+    return diff_bits(a.r, b.r) | diff_bits(a.mn, b.mn) | diff_bits(a.mt, b.mt) | diff_bits(a.E, b.E);
+}
+template <class T>
+__device__ __forceinline__ bool same_bits(const Cons<T>& a, const Cons<T>& b) {
+    return diff_bits(a, b) == 0;
+}
+
 // Status bits and (second sweep) CFL wave speed of one new cell state.
 template <class T, int WHICH>
 __device__ __forceinline__ void check_cell(const Consts<T>& K, const Cons<T>& out, unsigned& tbad, T& smax,
@@ -459,6 +473,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
         const unsigned pitch = (unsigned)g.pitch;
         YWalk<T> w = {};
         Cons<T> gsave = {};  // mirror of row n-2, kept for position n+1
+        int run = 1;         // positions ending at the current one with equal conserved bits
         T smax = T(0);
         unsigned sbits = 0;  // FP64: max FP32 speed estimate (float bits)
         unsigned tbad = 0;
@@ -481,6 +496,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                 if (kc + 1 < 0) u = y_ghost<T>(a.src, g, lsafe, kc + 1, n, bclo, bchi, sp, kc, lane, w, gsave);
                 w.u1 = u;
                 w.w1 = cons_to_prim(K, u, w.ir1);
+                run = (Shortcuts<T>::stencil && same_bits(w.u1, w.u0)) ? 2 : 1;
                 j0 = 2;
             }
             // one copy of the per-cell arithmetic: position k completes the
@@ -492,19 +508,41 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                 if (k > klast) break;
                 Cons<T> u = chunk_cell<T>(sp, j, lane);
                 if (k >= n) u = y_ghost<T>(a.src, g, lsafe, k, n, bclo, bchi, sp, kc, lane, w, gsave);
+                const bool same = Shortcuts<T>::stencil && same_bits(u, w.u1);
+                run = same ? run + 1 : 1;
+                // rows k-4..k equal bit for bit: the traces of k-3..k-1 return
+                // the cell, both interfaces of row k-2 are equal-state problems
+                // of that one state, so their fluxes are equal (fhi = flo) and
+                // the update returns row k-2 unchanged
+                const bool uniform = run >= 5 && k >= s0 + 2;
+                unsigned wk = kUniformWork;
                 T ir2;
-                const Prim<T> w2 = cons_to_prim(K, u, ir2);
-                Prim<T> wl1, wr1;
-                trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
-                // at k = s0 the face left of cell s0-1 is not formed: solve a
-                // trivial problem (equal states) whose flux is never used
-                if (k == s0) w.wr0 = wl1;
-                unsigned wk = 0;
-                const Cons<T> fhi = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb, wk);
+                Prim<T> w2, wr1;
+                Cons<T> fhi;
+                if (uniform) {
+                    w2 = w.w1;
+                    ir2 = w.ir1;
+                    wr1 = w.w1;
+                    fhi = w.flo;
+                } else {
+                    if (same) {  // the same conserved bits give the same primitives
+                        w2 = w.w1;
+                        ir2 = w.ir1;
+                    } else {
+                        w2 = cons_to_prim(K, u, ir2);
+                    }
+                    Prim<T> wl1;
+                    trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
+                    // at k = s0 the face left of cell s0-1 is not formed: solve
+                    // a trivial problem (equal states) whose flux is never used
+                    if (k == s0) w.wr0 = wl1;
+                    fhi = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb, wk);
+                }
                 // the warp's work at this row is that of its slowest lane
                 if (kRecord) tcost += __reduce_max_sync(0xffffffffu, wk);
                 if (k >= s0 + 2) {
-                    const Cons<T> out = update(w.u0, dtdx, fhi, w.flo);
+                    Cons<T> out = w.u0;
+                    if (!uniform) out = update(w.u0, dtdx, fhi, w.flo);
                     if (valid) {
                         const unsigned o = (unsigned)(k - 2) * pitch;
                         q0[o] = out.r;
@@ -710,6 +748,22 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
                 if (kA > n + 1) uA = ch;
                 if (kB > n + 1) uB = ch;
             }
+            const bool lo = inner && A >= 0 && A < n;
+            const bool hi = inner && A + 1 < n;
+            if (Shortcuts<T>::stencil) {
+                // all 64 cells of the segment equal bit for bit (ghosts and
+                // fill included): every stencil is uniform, the traces return
+                // the cells, all fluxes are equal and each result is its cell
+                const Cons<T> ref = shfl_idx(uA, 0);
+                if (__all_sync(0xffffffffu, (diff_bits(uA, ref) | diff_bits(uB, ref)) == 0)) {
+                    if (lo) {
+                        store_pair<T>(drow + A, g.plane, uA, uB, lo, hi);
+                        check_cell<T, WHICH>(K, uA, tbad, smax, sbits);
+                        if (hi) check_cell<T, WHICH>(K, uB, tbad, smax, sbits);
+                    }
+                    continue;
+                }
+            }
             T irA, irB;
             const Prim<T> WA = cons_to_prim(K, uA, irA);
             const Prim<T> WB = cons_to_prim(K, uB, irB);
@@ -732,8 +786,6 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
             const Cons<T> Fp = shfl_down1(Fm);                              // B + 1/2
             const Cons<T> nA = update(uA, dtdx, Fc, Fm);
             const Cons<T> nB = update(uB, dtdx, Fp, Fc);
-            const bool lo = inner && A >= 0 && A < n;
-            const bool hi = inner && A + 1 < n;
             // a second-pass request counts only for interfaces feeding stored cells
             redo |= (r1 || r2) && lo;
             if (lo) {
