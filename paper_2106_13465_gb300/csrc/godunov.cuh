@@ -47,6 +47,7 @@ struct Consts {
     int niter;    // maximum Newton iterations
     T bz[kBinomTerms];  // binomial coefficients C(z, k), k = 1 .. kBinomTerms
     T pz_series;        // (1 - kBinomRadius)^z: (p/p_K)^z below it came from exp2/log2
+    float f_gamma, f_gm1, f_rho_floor, f_cf2g;  // FP32 copies (the FP64 CFL estimate)
 };
 
 template <class T> struct Prim { T r, u, v, p; };     // u normal, v tangential

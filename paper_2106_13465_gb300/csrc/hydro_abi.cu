@@ -58,6 +58,10 @@ Consts<T> make_consts(const hydro_params& p, double tol) {
         K.bz[k - 1] = (T)c;
     }
     K.pz_series = (T)std::pow(1.0 - kBinomRadius, z);
+    K.f_gamma = (float)g;
+    K.f_gm1 = (float)(g - 1.0);
+    K.f_rho_floor = (float)p.rho_floor;
+    K.f_cf2g = (float)(p.c_floor * p.c_floor / g);
     return K;
 }
 

@@ -258,7 +258,7 @@ __device__ __forceinline__ float f32_trunc(double x) {
 // estimate (overflow, NaN input) sends every cell of the grid to the exact
 // evaluation.
 __device__ __forceinline__ float cfl_estimate(const Consts<double>& K, double r, double mn, double mt, double E) {
-    const float rfl = (float)K.rho_floor, gm1 = (float)K.gm1, gam = (float)K.gamma, cf2g = (float)K.cf2g;
+    const float rfl = K.f_rho_floor, gm1 = K.f_gm1, gam = K.f_gamma, cf2g = K.f_cf2g;
     float rho = f32_trunc(r);
     rho = (rho < rfl) ? rfl : rho;
     const float ir = 1.0f / rho;
@@ -474,6 +474,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
         YWalk<T> w = {};
         Cons<T> gsave = {};  // mirror of row n-2, kept for position n+1
         int run = 1;         // positions ending at the current one with equal conserved bits
+        bool copied = false; // the previous row was a copy (uniform stencil)
         T smax = T(0);
         unsigned sbits = 0;  // FP64: max FP32 speed estimate (float bits)
         unsigned tbad = 0;
@@ -519,12 +520,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                 T ir2;
                 Prim<T> w2, wr1;
                 Cons<T> fhi;
-                if (uniform) {
-                    w2 = w.w1;
-                    ir2 = w.ir1;
-                    wr1 = w.w1;
-                    fhi = w.flo;
-                } else {
+                if (!uniform) {
                     if (same) {  // the same conserved bits give the same primitives
                         w2 = w.w1;
                         ir2 = w.ir1;
@@ -540,6 +536,12 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                 }
                 // the warp's work at this row is that of its slowest lane
                 if (kRecord) tcost += __reduce_max_sync(0xffffffffu, wk);
+                if (uniform) {  // the window rotates equal states
+                    w2 = w.w1;
+                    ir2 = w.ir1;
+                    wr1 = w.w1;
+                    fhi = w.flo;
+                }
                 if (k >= s0 + 2) {
                     Cons<T> out = w.u0;
                     if (!uniform) out = update(w.u0, dtdx, fhi, w.flo);
@@ -549,9 +551,12 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                         qn[o] = out.mn;
                         qt[o] = out.mt;
                         qe[o] = out.E;
-                        check_cell<T, WHICH>(K, out, tbad, smax, sbits);
+                        // a copy equal to the previous row's copy has its
+                        // status and wave speed already counted
+                        if (!(uniform && copied)) check_cell<T, WHICH>(K, out, tbad, smax, sbits);
                     }
                 }
+                copied = uniform;
                 w.flo = fhi;
                 w.u0 = w.u1;
                 w.w0 = w.w1;
@@ -756,10 +761,11 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
                 // the cells, all fluxes are equal and each result is its cell
                 const Cons<T> ref = shfl_idx(uA, 0);
                 if (__all_sync(0xffffffffu, (diff_bits(uA, ref) | diff_bits(uB, ref)) == 0)) {
+                    // one status and wave-speed check stands for all the copies
+                    const int first = __ffs(__ballot_sync(0xffffffffu, lo)) - 1;
                     if (lo) {
                         store_pair<T>(drow + A, g.plane, uA, uB, lo, hi);
-                        check_cell<T, WHICH>(K, uA, tbad, smax, sbits);
-                        if (hi) check_cell<T, WHICH>(K, uB, tbad, smax, sbits);
+                        if (lane == first) check_cell<T, WHICH>(K, uA, tbad, smax, sbits);
                     }
                     continue;
                 }
