@@ -98,8 +98,8 @@ typedef struct {
  * best makespan of a list-scheduling model of the tile queue on the
  * resident warps (uniform cost per cell).  In FP64 contexts tile_len = 0
  * also makes the y tiles adaptive: every y sweep records an estimate of the
- * work (Newton iterations, powers) spent on each block of 4 rows of each
- * 32-column group, and before the next y sweep the library splits each
+ * work (Newton iterations, powers, copies of uniform rows) spent on each row
+ * of each 32-column group, and before the next y sweep the library splits each
  * model tile into pieces whose recorded work stays below the mean work
  * of a model tile (pieces of at least half that work are queued first), so
  * regions where the Riemann solver works harder get shorter tiles.  The

@@ -54,7 +54,7 @@ enum { STATUS_BAD_RHO = 1u, STATUS_BAD_E = 2u, STATUS_TIMEOUT = 4u, STATUS_BAD_T
 enum { VAR_F64 = 0, VAR_F32_MAIN = 1, VAR_F32_REDO = 2 };
 
 constexpr int kWarpLines = 32;      // lines per warp tile (one per lane)
-constexpr int kYBlock = 4;          // rows per cost block of the adaptive y tiles
+constexpr int kYBlock = 1;          // rows per cost block of the adaptive y tiles
 constexpr double kYCostCap = 1.0;   // adaptive y tile work cap / mean static tile work
 constexpr double kYBigJob = 0.5;    // adaptive y tiles queued first: work / mean static tile work
 constexpr int kSweepThreads = 128;  // threads per CTA of the sweep kernels
