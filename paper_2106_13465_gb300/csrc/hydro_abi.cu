@@ -98,8 +98,8 @@ struct hydro_ctx {
     int* d_redo = nullptr;          // [2][redo_cap] FP32 second-pass tile lists
     float* d_ycost = nullptr;       // recorded y-sweep cost per block (adaptive y tiles)
     Tile* d_ystat = nullptr;        // static y tiling the adaptive tiles split
-    Strip* d_strips = nullptr;      // row strips of the FP64 CFL passes
-    int nstrips = 0;
+    unsigned int* d_tile_smax = nullptr;  // FP64: max speed estimate per tile of a second sweep
+    int tile_smax_cap = 0;
     int nystat = 0;
     long long nyblocks = 0;         // cost blocks of all grids
     bool y_adaptive = false;        // y tiles cut from recorded costs every step
@@ -352,6 +352,16 @@ hydro_status upload_tiles(hydro_ctx* c) {
             c->ctas_redo[d] = std::max(1, std::min(need, c->nsm * occ2));
         }
     }
+    if (c->prec == 64) {
+        const int cap = std::max(c->ntiles[0], c->ntiles[1]);
+        if (cap > c->tile_smax_cap) {
+            cudaFree(c->d_tile_smax);
+            c->d_tile_smax = nullptr;
+            c->tile_smax_cap = 0;
+            HCK(c, cudaMalloc(&c->d_tile_smax, sizeof(unsigned int) * (size_t)cap));
+            c->tile_smax_cap = cap;
+        }
+    }
     if (c->prec == 32) {
         const int cap = std::max(c->ntiles[0], c->ntiles[1]);
         if (cap > c->redo_cap) {
@@ -383,6 +393,7 @@ SweepArgs<T> sweep_args(hydro_ctx* c, int which, const Consts<T>& K) {
     a.ngrids = (int)c->gd.size();
     a.ntiles_dev = nullptr;
     a.ycost = c->d_ycost;
+    a.tile_smax = c->d_tile_smax;
     a.which = which;
     a.src_buf = which;
     a.redo_list = c->d_redo;
@@ -420,8 +431,8 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
             e = launch_sweep<T>(dir, VAR_F64, a, c->ctas[dir], s);
             // the second sweep's new state: its max wave speed (next dt)
             if (e == cudaSuccess && which == 1)
-                e = launch_cfl_fp64((const double*)c->buf[0], c->d_grids, c->d_strips, c->nstrips, c->d_run,
-                                    c->d_ctr, c->Kd, c->nsm * 8, s);
+                e = launch_cfl_fp64((const double*)c->buf[0], c->d_grids, a.tiles, a.ntiles, a.ntiles_dev, dir,
+                                    c->d_tile_smax, c->d_run, c->d_ctr, c->Kd, c->nsm * 8, s);
         } else {
             // main FP32 pass, then the second pass over tiles it queued
             e = launch_sweep<T>(dir, VAR_F32_MAIN, a, c->ctas[dir], s);
@@ -580,20 +591,6 @@ hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
         (st = alloc((void**)&c->d_stage, sizeof(double) * 4 * max_cells, "staging")) != HYDRO_OK)
         return bail(st);
     if ((st = alloc((void**)&c->d_ycost, sizeof(float) * c->nyblocks, "y cost blocks")) != HYDRO_OK) return bail(st);
-    {
-        // the FP64 CFL pass walks the grids in strips of whole rows, ~2048 cells each
-        std::vector<Strip> strips;
-        for (int g = 0; g < (int)c->gd.size(); ++g) {
-            const GridDesc& d = c->gd[g];
-            const int rows = std::max(1, std::min(d.ny, 2048 / d.nx));
-            for (int r = 0; r < d.ny; r += rows) strips.push_back(Strip{g, r, std::min(rows, d.ny - r), 0});
-        }
-        c->nstrips = (int)strips.size();
-        if ((st = alloc((void**)&c->d_strips, sizeof(Strip) * strips.size(), "cfl strips")) != HYDRO_OK) return bail(st);
-        e = cudaMemcpy(c->d_strips, strips.data(), sizeof(Strip) * strips.size(), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) { fail_cuda(c, "cfl strips upload", e); return bail(HYDRO_ECUDA); }
-    }
-
     e = cudaMemcpy(c->d_grids, c->gd.data(), sizeof(GridDesc) * c->gd.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_run, 0, sizeof(GridRun) * c->gd.size());
     if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, sizeof(DevCounters));
@@ -626,7 +623,7 @@ void hydro_destroy(hydro_ctx* c) {
     cudaFree(c->d_redo);
     cudaFree(c->d_ycost);
     cudaFree(c->d_ystat);
-    cudaFree(c->d_strips);
+    cudaFree(c->d_tile_smax);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -99,10 +99,6 @@ struct GridRun {
                                  // speed of the step's new state (bits of a float)
 };
 
-// A run of whole rows of one grid (the CFL passes of FP64 contexts).
-struct Strip {
-    int grid, row0, nrows, pad;
-};
 
 // Context-wide device counters.
 struct DevCounters {
@@ -131,6 +127,7 @@ struct SweepArgs {
     const unsigned int* ntiles_dev;  // adaptive y tiles: the two counts on the device
                                      // (ntiles is then the capacity of the list)
     float* ycost;                    // y sweep: per-block work recorded here
+    unsigned int* tile_smax;         // FP64 second sweep: max FP32 speed estimate per tile
     int which;       // 0: first sweep of the step, 1: second (folds in CFL max)
     int src_buf;     // buffer index of src (its tensor maps)
     int* redo_list;  // [2][redo_cap] tile indices for the FP32 second pass
@@ -148,14 +145,18 @@ int sweep_ctas_per_sm(int dir, int var);
 
 // ---- launchers (defined in the kernel translation units) ------------------
 // FP64 contexts: the max wave speed of the state a step produced.  The
-// second sweep keeps the per-grid max M of an FP32 estimate of every new
-// cell's speed (smax32); this pass over the strips then evaluates the exact
-// FP64 speed of every cell whose estimate is not below M (1 - kCflScreen)
-// (all cells if M is not finite) and folds it into wmax[acc].  The estimate
-// is within 2e-3 of the exact speed (relative), well inside kCflScreen / 2,
-// so the cell of the exact maximum is always among those evaluated in FP64.
+// second sweep keeps the max M of an FP32 estimate of every new cell's speed
+// per grid (smax32) and per tile (tile_smax); this pass then visits the tiles
+// of that sweep whose own max is not below M (1 - kCflScreen) (every tile if
+// M is not finite), evaluates the exact FP64 speed of each of their cells
+// whose estimate is not below that bound, and folds it into wmax[acc].  The
+// estimate is within 2e-3 of the exact speed (relative), well inside
+// kCflScreen / 2, so the cell of the exact maximum is always evaluated.
+// tiles / ntiles / ntiles_dev / dir describe the second sweep's work list as
+// in SweepArgs.
 constexpr float kCflScreen = 1e-2f;
-cudaError_t launch_cfl_fp64(const double* state, const GridDesc* grids, const Strip* strips, int nstrips,
+cudaError_t launch_cfl_fp64(const double* state, const GridDesc* grids, const Tile* tiles, int ntiles,
+                            const unsigned int* ntiles_dev, int dir, const unsigned int* tile_smax,
                             GridRun* run, const DevCounters* ctr, const Consts<double>& K, int nctas,
                             cudaStream_t s);
 

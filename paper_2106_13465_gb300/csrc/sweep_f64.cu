@@ -21,44 +21,57 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-// After the second sweep, which left M = the grid's max FP32 speed estimate
-// in smax32: the exact FP64 speed of every cell whose estimate is not below
-// M (1 - kCflScreen) (every cell if M is not finite), folded into wmax[acc]
-// (bits of non-negative doubles order as unsigned integers).
+// One warp per tile of the second sweep (a warp-strided loop over the list).
 __global__ void __launch_bounds__(256) cfl_refine_kernel(const double* __restrict__ st,
                                                          const GridDesc* __restrict__ grids,
-                                                         const Strip* __restrict__ strips, int nstrips,
+                                                         const Tile* __restrict__ tiles, int ntiles,
+                                                         const unsigned int* ntiles_dev, int dir,
+                                                         const unsigned int* __restrict__ tile_smax,
                                                          GridRun* run, const DevCounters* ctr, Consts<double> K) {
     const unsigned acc = ctr->acc;
     const int lane = threadIdx.x & 31;
-    for (int si = blockIdx.x; si < nstrips; si += gridDim.x) {
-        const Strip sp = strips[si];
-        const GridDesc g = grids[sp.grid];
-        const float M = __uint_as_float(run[sp.grid].smax32);
-        const float thr = isfinite(M) ? M * (1.0f - kCflScreen) : 0.0f;
+    const unsigned nf = ntiles_dev ? ntiles_dev[0] : (unsigned)ntiles;
+    const unsigned nb = ntiles_dev ? ntiles_dev[1] : 0u;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nf + nb; i += nwarps) {
+        const int t = (i < nf) ? (int)i : ntiles - 1 - (int)(i - nf);
+        const Tile tile = tiles[t];
+        const float M = __uint_as_float(run[tile.grid].smax32);
+        const bool all = !isfinite(M);
+        const float thr = all ? 0.0f : M * (1.0f - kCflScreen);
+        if (!all && __uint_as_float(tile_smax[t]) < thr) continue;  // no cell near the max
+        const GridDesc g = grids[tile.grid];
         unsigned long long m = 0ull;
-        const int n = sp.nrows * g.nx;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int dj = k / g.nx, i = k - dj * g.nx;
-            const double* q = st + g.off + (long long)(sp.row0 + dj) * g.pitch + i;
+        auto visit = [&](int i, int j) {
+            const double* q = st + g.off + (long long)j * g.pitch + i;
             const double r = q[0], mn = q[g.plane], mt = q[2 * g.plane], E = q[3 * g.plane];
             if (!(cfl_estimate(K, r, mn, mt, E) < thr)) {
                 const double w = cfl_speed(K, Cons<double>{r, mn, mt, E});
                 const unsigned long long b = (unsigned long long)__double_as_longlong(w);
                 m = (b > m) ? b : m;
             }
+        };
+        if (dir == DIR_X) {
+            // segments cell0 .. cell0 + ncell - 1 of row line0: results [60k - 2, 60k + 58)
+            const int x0 = max(0, kXStride * tile.cell0 - 2);
+            const int x1 = min(g.nx, kXStride * (tile.cell0 + tile.ncell) - 2);
+            for (int x = x0 + lane; x < x1; x += 32) visit(x, tile.line0);
+        } else {
+            const int col = tile.line0 + lane;
+            if (col < g.nx)
+                for (int j = tile.cell0; j < tile.cell0 + tile.ncell; ++j) visit(col, j);
         }
         m = warp_max_u64(m);
-        if (lane == 0 && m) atomicMax(&run[sp.grid].wmax[acc], m);
+        if (lane == 0 && m) atomicMax(&run[tile.grid].wmax[acc], m);
     }
 }
 
-cudaError_t launch_cfl_fp64(const double* state, const GridDesc* grids, const Strip* strips, int nstrips,
+cudaError_t launch_cfl_fp64(const double* state, const GridDesc* grids, const Tile* tiles, int ntiles,
+                            const unsigned int* ntiles_dev, int dir, const unsigned int* tile_smax,
                             GridRun* run, const DevCounters* ctr, const Consts<double>& K, int nctas,
                             cudaStream_t s) {
-    if (nstrips <= 0) return cudaSuccess;
-    const int blocks = nctas < nstrips ? nctas : nstrips;
-    cfl_refine_kernel<<<blocks, 256, 0, s>>>(state, grids, strips, nstrips, run, ctr, K);
+    if (ntiles <= 0) return cudaSuccess;
+    cfl_refine_kernel<<<nctas, 256, 0, s>>>(state, grids, tiles, ntiles, ntiles_dev, dir, tile_smax, run, ctr, K);
     return cudaGetLastError();
 }
 

@@ -309,9 +309,13 @@ __device__ __forceinline__ void finish_tile(const SweepArgs<T>& a, int t, int gr
     }
     kbad |= tbad;
     if (WHICH == 1 && sizeof(T) == 8) {
-        // FP64: max of the FP32 speed estimates (bits order as unsigned)
+        // FP64: max of the FP32 speed estimates (bits order as unsigned), per
+        // grid and per tile (the CFL pass visits only tiles near the max)
         const unsigned m = __reduce_max_sync(0xffffffffu, sbits);
-        if (lane == 0 && m) atomicMax(&a.run[grid].smax32, m);
+        if (lane == 0) {
+            a.tile_smax[t] = m;
+            if (m) atomicMax(&a.run[grid].smax32, m);
+        }
     }
     if (WHICH == 1 && sizeof(T) == 4) {
         double m = (double)smax;
