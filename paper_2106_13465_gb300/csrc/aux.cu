@@ -140,6 +140,7 @@ cudaError_t launch_retile_y(const GridDesc* grids, const Tile* stat, int nstat, 
 // ---- CFL speed of a loaded state ------------------------------------------
 __global__ void cfl_zero_kernel(GridRun* run, int grid, const DevCounters* ctr) {
     run[grid].wmax[ctr->acc] = 0ull;
+    run[grid].smax32 = 0u;
 }
 
 template <class T>
@@ -169,6 +170,8 @@ cudaError_t launch_cfl_init(const T* state, const GridDesc* grids, int grid, con
                             GridRun* run, DevCounters* ctr, Consts<T> K, cudaStream_t s) {
     (void)grids;
     cfl_zero_kernel<<<1, 1, 0, s>>>(run, grid, ctr);
+    // FP64: an FP32 screen, then the exact speed near its maximum only
+    if constexpr (sizeof(T) == 8) return launch_cfl_screened_fp64(state, gd, grid, run, ctr, K, s);
     const long long ncell = (long long)gd.nx * gd.ny;
     long long nb = (ncell + 255) / 256;
     if (nb > 4096) nb = 4096;

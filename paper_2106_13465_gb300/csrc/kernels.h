@@ -160,6 +160,13 @@ cudaError_t launch_cfl_fp64(const double* state, const GridDesc* grids, const Ti
                             GridRun* run, const DevCounters* ctr, const Consts<double>& K, int nctas,
                             cudaStream_t s);
 
+// The max wave speed of one FP64 grid's state (an uploaded state): the same
+// screen as launch_cfl_fp64 over every cell (max FP32 estimate M), then the
+// exact FP64 speed of the cells within kCflScreen of M, into wmax[acc].  run's
+// slots of the grid must be zero.
+cudaError_t launch_cfl_screened_fp64(const double* state, const GridDesc& gd, int grid, GridRun* run,
+                                     const DevCounters* ctr, const Consts<double>& K, cudaStream_t s);
+
 template <class T>
 cudaError_t launch_sweep(int dir, int var, const SweepArgs<T>& a, int nctas, cudaStream_t s);
 

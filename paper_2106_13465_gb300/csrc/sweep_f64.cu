@@ -75,6 +75,50 @@ cudaError_t launch_cfl_fp64(const double* state, const GridDesc* grids, const Ti
     return cudaGetLastError();
 }
 
+// Whole-grid screen (PASS 0: max FP32 estimate into smax32) and exact pass
+// (PASS 1: FP64 speed of the cells near that max into wmax[acc]).
+template <int PASS>
+__global__ void __launch_bounds__(256) cfl_grid_kernel(const double* __restrict__ st, GridDesc g, int grid,
+                                                       GridRun* run, const DevCounters* ctr, Consts<double> K) {
+    float thr = 0.0f;
+    if (PASS == 1) {
+        const float M = __uint_as_float(run[grid].smax32);
+        thr = isfinite(M) ? M * (1.0f - kCflScreen) : 0.0f;
+    }
+    unsigned long long m = 0ull;
+    const long long ncell = (long long)g.nx * g.ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(c / g.nx), i = (int)(c - (long long)j * g.nx);
+        const double* q = st + g.off + (long long)j * g.pitch + i;
+        const double r = q[0], mn = q[g.plane], mt = q[2 * g.plane], E = q[3 * g.plane];
+        const float e = cfl_estimate(K, r, mn, mt, E);
+        if (PASS == 0) {
+            const unsigned long long b = __float_as_uint(e);
+            m = (b > m) ? b : m;
+        } else if (!(e < thr)) {
+            const unsigned long long b =
+                (unsigned long long)__double_as_longlong(cfl_speed(K, Cons<double>{r, mn, mt, E}));
+            m = (b > m) ? b : m;
+        }
+    }
+    m = warp_max_u64(m);
+    if ((threadIdx.x & 31) == 0 && m) {
+        if (PASS == 0) atomicMax(&run[grid].smax32, (unsigned)m);
+        else atomicMax(&run[grid].wmax[ctr->acc], m);
+    }
+}
+
+cudaError_t launch_cfl_screened_fp64(const double* state, const GridDesc& gd, int grid, GridRun* run,
+                                     const DevCounters* ctr, const Consts<double>& K, cudaStream_t s) {
+    const long long ncell = (long long)gd.nx * gd.ny;
+    long long nb = (ncell + 255) / 256;
+    if (nb > 4096) nb = 4096;
+    cfl_grid_kernel<0><<<(int)nb, 256, 0, s>>>(state, gd, grid, run, ctr, K);
+    cfl_grid_kernel<1><<<(int)nb, 256, 0, s>>>(state, gd, grid, run, ctr, K);
+    return cudaGetLastError();
+}
+
 template <>
 int sweep_ctas_per_sm<double>(int dir, int var) {
     (void)var;
