@@ -345,7 +345,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # ---- roofline of the dominant kernel (the sweep) ----------------------
     peaks = load_peaks()
     prof = recorded_profile(wl)
-    alg_bytes = float(state_bytes)  # one read + one write of 4 planes per sweep = 2 x (state / 2)
+    alg_bytes = 2.0 * 4 * esz * cells  # one read + one write of the 4 planes of every cell per sweep
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     hbm_achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
     hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
