@@ -122,6 +122,23 @@ def test_uniform_state_bit_exact_on_gpu():
         assert dts[0] == pytest.approx(0.8 * pb.h / (max(abs(u), abs(v)) + c), rel=1e-15)
 
 
+@pytest.mark.parametrize("bc", [(R_,) * 4, (T_, R_, P_, P_)])
+def test_uniform_flow_meeting_walls_and_a_small_disturbance(bc):
+    """A uniform moving gas (most cells are copied by the uniform-stencil
+    paths) that runs into reflective walls and carries one perturbed cell:
+    the waves it creates, and the copies around them, match the oracle."""
+    pb = pr.uniform(150, 131, rho=0.8, u=0.3, v=-0.2, p=1.7, bc=bc)
+    U = pb.U.copy()
+    U[3, 60, 70] *= 1.5   # a small energy bump away from the walls
+    U[0, 20, 5] *= 1.1    # and a density bump near the x low wall
+    pb = pr.Problem("moving", U, pb.h, bc)
+    for n in (3, 24):
+        want, odts, _ = O.run(pb.U, pb.h, pb.bc, n)
+        got, gdts, _ = gpu_run(pb, n)
+        assert rel_err(got, want) <= TOL64, n
+        assert np.allclose(gdts, odts, rtol=1e-12, atol=0)
+
+
 @pytest.mark.parametrize("precision", [64, 32])
 def test_results_identical_for_every_tile_shape_schedule_and_graph(precision):
     pb = pr.random_modes(150, 97, seed=21)
