@@ -164,9 +164,17 @@ struct FluxOp<float, VAR_F32_REDO> {
 
 
 // ------------------------------------------------------------ helpers -----
+// Mirror image of a state about a reflective wall: the normal momentum is
+// negated as 0 - m, which equals -m except that a zero momentum stays +0.  A
+// gas at rest then mirrors to bitwise the same state, so the equal-state and
+// uniform-stencil shortcuts hold across the wall (with -m the +-0 pair forces
+// a full Riemann solve at every wall interface, whose result only differs in
+// the sign of zeros).
+__device__ __forceinline__ double neg0(double m) { return __dsub_rn(0.0, m); }
+__device__ __forceinline__ float neg0(float m) { return __fsub_rn(0.0f, m); }
 template <class T>
 __device__ __forceinline__ Cons<T> flip(Cons<T> u, bool f) {
-    if (f) u.mn = -u.mn;
+    if (f) u.mn = neg0(u.mn);
     return u;
 }
 
