@@ -45,6 +45,7 @@ struct Consts {
     T pmin;       // smallest pressure of the Riemann iteration, rho_floor * cf2g
     T tol;        // Newton convergence test |p_new - p| <= tol * p_new
     int niter;    // maximum Newton iterations
+    int g75;      // g = 7/5: z = 1/7, G4 = 5, G3 = 7 (a 7th root and integer powers)
     T bz[kBinomTerms];  // binomial coefficients C(z, k), k = 1 .. kBinomTerms
     T pz_series;        // (1 - kBinomRadius)^z: (p/p_K)^z below it came from exp2/log2
     float f_gamma, f_gm1, f_rho_floor, f_cf2g;  // FP32 copies (the FP64 CFL estimate)
@@ -70,7 +71,42 @@ __device__ __forceinline__ float tabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
 
-// (p / p_K)^z, given 1/p_K.  FP64: where x = (p - p_K)/p_K has |x| <= 0.01,
+// x^(1/7) for a positive normal double, within 3 ulp (a 7th root by Newton's
+// method for nth roots, taken to third order):  write x = m 2^(7q) with m in
+// [1, 2^7); v0 ~ m^(-1/7) from the FP32 hardware log2 and exp2 (relative
+// error below 1e-6); h = m v0^7 - 1 with one rounding (fused multiply-add);
+// then m^(1/7) = m v0^6 (1 + h)^(-6/7), the binomial series to h^3 (the
+// remainder is below 1e-22) -- ten FP64 operations, no division.  A rounding
+// error d in v0^6 moves the result by only d/7, since it enters h as well.
+// The exponent q is added to the result's exponent field.  Other x: exp2/log2.
+__device__ __forceinline__ double root7(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int ex = (int)((hi >> 20) & 0x7ffu);
+    if (ex == 0 || ex == 0x7ff) return exp2(log2(x) * (1.0 / 7.0));
+    const int e = ex - 1023;
+    const int q = (e + 1029) / 7 - 147;  // floor(e / 7) for e in [-1022, 1023]
+    const int r = e - 7 * q;             // 0 .. 6
+    const unsigned mant = hi & 0x000fffffu;
+    const double m = __hiloint2double((int)(mant | ((unsigned)(1023 + r) << 20)), (int)lo);
+    const float mf = __uint_as_float(((unsigned)(127 + r) << 23) | (mant << 3) | (lo >> 29));
+    float t;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(mf));
+    t = t * (-1.0f / 7.0f);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(t));
+    // t in (1/2, 1]: exact conversion to double on the integer pipe
+    const unsigned fb = __float_as_uint(t);
+    const double v0 = __hiloint2double((int)((((fb >> 23) + (1023u - 127u)) << 20) | ((fb & 0x7fffffu) >> 3)),
+                                       (int)(fb << 29));
+    const double v2 = v0 * v0, v3 = v2 * v0, v6 = v3 * v3, v7 = v6 * v0;
+    const double h = fma(m, v7, -1.0);
+    const double P = fma(fma(h, -260.0 / 343.0, 39.0 / 49.0), h, -6.0 / 7.0);  // (1+h)^(-6/7) = 1 + h P
+    const double base = m * v6;
+    const double y = fma(base, h * P, base);
+    return __hiloint2double((int)((unsigned)__double2hiint(y) + ((unsigned)q << 20)), __double2loint(y));
+}
+
+// (p / p_K)^z, given 1/p_K.  FP64 with g = 7/5: the 7th root of p/p_K.
+// Other FP64: where x = (p - p_K)/p_K has |x| <= 0.01,
 // the binomial series (1 + x)^z = sum_k C(z, k) x^k summed to k = 8 by
 // Horner's rule; for 0 < z < 1/2 the remainder is below 0.5 * 0.01^9, far
 // under one unit in the last place; p = p_K gives 1 exactly.  This is the
@@ -80,7 +116,8 @@ __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a
 template <class T>
 __device__ __forceinline__ T pow_z(const Consts<T>& K, T p, T pK, T ip) {
     if (p == pK) return T(1);
-    if (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8) {
+        if (K.g75) return root7(p * ip);
         const T x = (p - pK) * ip;
         if (tabs(x) <= T(kBinomRadius)) {
             T s = K.bz[kBinomTerms - 1];
@@ -401,8 +438,14 @@ __device__ __forceinline__ Prim<T> sample_side(const Consts<T>& K, const Side<T>
                 const T c = K.G5 * tfma(sgn * K.G7, S.u, S.c);
                 const T cc = c / S.c;
                 W.u = sgn * c;
-                W.r = S.r * tpow(cc, K.G4);
-                W.p = S.p * tpow(cc, K.G3);
+                if (K.g75) {  // (c/c_K)^5 and (c/c_K)^7
+                    const T c2 = cc * cc, c5 = c2 * c2 * cc;
+                    W.r = S.r * c5;
+                    W.p = S.p * (c5 * c2);
+                } else {
+                    W.r = S.r * tpow(cc, K.G4);
+                    W.p = S.p * tpow(cc, K.G3);
+                }
             }
         }
     }

@@ -52,12 +52,15 @@ Consts<T> make_consts(const hydro_params& p, double tol) {
     K.pmin = (T)(p.rho_floor * (p.c_floor * p.c_floor / g));
     K.tol = (T)tol;
     K.niter = p.niter_riemann;
+    K.g75 = (g == 1.4) ? 1 : 0;
     double c = 1.0, z = (g - 1.0) / (2.0 * g);
     for (int k = 1; k <= kBinomTerms; ++k) {
         c *= (z - (k - 1)) / k;  // C(z, k)
         K.bz[k - 1] = (T)c;
     }
-    K.pz_series = (T)std::pow(1.0 - kBinomRadius, z);
+    // below it (p/p_K)^z came from exp2/log2 (the 7th root for g = 7/5 costs
+    // no more than the series, so 0 there)
+    K.pz_series = K.g75 ? (T)0 : (T)std::pow(1.0 - kBinomRadius, z);
     K.f_gamma = (float)g;
     K.f_gm1 = (float)(g - 1.0);
     K.f_rho_floor = (float)p.rho_floor;
