@@ -22,6 +22,7 @@ __global__ void step_prologue_kernel(GridRun* run, const GridDesc* grids, int ng
         run[g].smax32 = 0u;
         if (dt_log) dt_log[g] = dt;
     }
+    for (int i = threadIdx.x; i < kMaxSmIds; i += blockDim.x) ctr->sm_slot[i] = 0u;
     __syncthreads();
     if (threadIdx.x == 0) {
         ctr->acc = dst;

@@ -100,6 +100,7 @@ struct hydro_ctx {
     CUtensorMap* d_maps = nullptr;  // [grid][buffer][dir]
     int* d_redo = nullptr;          // [2][redo_cap] FP32 second-pass tile lists
     float* d_ycost = nullptr;       // recorded y-sweep cost per block (adaptive y tiles)
+    unsigned long long* d_yclaim = nullptr;  // claim words of the adaptive y tiles
     Tile* d_ystat = nullptr;        // static y tiling the adaptive tiles split
     unsigned int* d_tile_smax = nullptr;  // FP64: max speed estimate per tile of a second sweep
     int tile_smax_cap = 0;
@@ -337,6 +338,11 @@ hydro_status upload_tiles(hydro_ctx* c) {
             c->tile_len_used[d] = 0;
             HCK(c, cudaMalloc(&c->d_tiles[d], sizeof(Tile) * (size_t)c->nyblocks));
             c->ntiles[d] = (int)std::min<long long>(c->nyblocks, 1LL << 30);
+            // claim words start below every step count (steps count from 1)
+            if (c->d_yclaim) cudaFree(c->d_yclaim);
+            c->d_yclaim = nullptr;
+            HCK(c, cudaMalloc(&c->d_yclaim, sizeof(unsigned long long) * (size_t)c->nyblocks));
+            HCK(c, cudaMemset(c->d_yclaim, 0, sizeof(unsigned long long) * (size_t)c->nyblocks));
         } else {
             if (d == DIR_Y) c->y_adaptive = false;
             const int L = chosen > 0 ? chosen : auto_tile_len(c->gd, d, resident_warps);
@@ -395,6 +401,8 @@ SweepArgs<T> sweep_args(hydro_ctx* c, int which, const Consts<T>& K) {
     a.ntiles = 0;
     a.ngrids = (int)c->gd.size();
     a.ntiles_dev = nullptr;
+    a.yclaim = nullptr;
+    a.nsm = c->nsm;
     a.ycost = c->d_ycost;
     a.tile_smax = c->d_tile_smax;
     a.which = which;
@@ -429,7 +437,10 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
         SweepArgs<T> a = sweep_args<T>(c, which, K);
         a.tiles = c->d_tiles[dir];
         a.ntiles = c->ntiles[dir];
-        if (dir == DIR_Y && c->y_adaptive) a.ntiles_dev = c->d_ctr->ytiles;
+        if (dir == DIR_Y && c->y_adaptive) {
+            a.ntiles_dev = c->d_ctr->ytiles;
+            a.yclaim = c->d_yclaim;
+        }
         if (sizeof(T) == 8) {
             e = launch_sweep<T>(dir, VAR_F64, a, c->ctas[dir], s);
             // the second sweep's new state: its max wave speed (next dt)
@@ -625,6 +636,7 @@ void hydro_destroy(hydro_ctx* c) {
     cudaFree(c->d_maps);
     cudaFree(c->d_redo);
     cudaFree(c->d_ycost);
+    cudaFree(c->d_yclaim);
     cudaFree(c->d_ystat);
     cudaFree(c->d_tile_smax);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);

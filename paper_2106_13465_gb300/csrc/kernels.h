@@ -100,6 +100,9 @@ struct GridRun {
 };
 
 
+// SM ids below this bound spread the long adaptive y tiles (see claim_tile).
+constexpr int kMaxSmIds = 256;
+
 // Context-wide device counters.
 struct DevCounters {
     unsigned int acc;            // wmax slot holding the current state's speed
@@ -113,6 +116,7 @@ struct DevCounters {
                                           // list holds ytiles[0] long jobs from its
                                           // front and ytiles[1] short ones from its back
     unsigned long long ycost_total[2];    // recorded y-sweep work, by step parity
+    unsigned int sm_slot[kMaxSmIds];      // y sweep: warps that have started on each SM
 };
 
 template <class T>
@@ -126,6 +130,9 @@ struct SweepArgs {
     int ngrids;
     const unsigned int* ntiles_dev;  // adaptive y tiles: the two counts on the device
                                      // (ntiles is then the capacity of the list)
+    unsigned long long* yclaim;      // adaptive y tiles: step count at which each long
+                                     // job was last claimed (each taken once per step)
+    int nsm;                         // SMs of the device
     float* ycost;                    // y sweep: per-block work recorded here
     unsigned int* tile_smax;         // FP64 second sweep: max FP32 speed estimate per tile
     int which;       // 0: first sweep of the step, 1: second (folds in CFL max)

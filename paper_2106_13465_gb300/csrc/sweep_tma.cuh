@@ -280,23 +280,43 @@ __device__ __forceinline__ float cfl_estimate(const Consts<double>& K, double r,
 
 // Claim the next tile: the main pass takes the work list in order, the FP32
 // second pass takes the tiles the main pass queued.  -1 when none is left.
+//
+// Adaptive y tiles (FP64): long jobs from the front of the list, then short
+// ones from its back.  The long jobs are the few heavy Riemann problems of a
+// sweep, and two of them on one SM share its FP64 pipe, so a warp's first
+// claim spreads them: the s-th warp to start on SM m takes long job
+// s * nsm + m, if nobody has.  Every long job also stays in the counter's
+// order, and a job is taken by whoever first swaps the step count `ep` into
+// its claim word, so each is taken exactly once however many warps an SM
+// runs.
 template <class T, int VAR>
-__device__ __forceinline__ int claim_tile(const SweepArgs<T>& a, int lane) {
-    int t = 0;
+__device__ __forceinline__ int claim_tile(const SweepArgs<T>& a, int lane, bool first = false,
+                                          unsigned long long ep = 0) {
+    int t = -1;
     if (lane == 0) {
         if (VAR == VAR_F32_REDO) {
             const unsigned i = atomicAdd(&a.ctr->redo_claim[a.which], 1u);
             t = (i < a.ctr->redo_count[a.which]) ? a.redo_list[a.which * a.redo_cap + i] : -1;
+        } else if (a.ntiles_dev) {
+            const unsigned nf = a.ntiles_dev[0], nb = a.ntiles_dev[1];
+            if (first && a.yclaim) {
+                unsigned sm;
+                asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+                if (sm < (unsigned)kMaxSmIds) {
+                    const unsigned long long j =
+                        (unsigned long long)atomicAdd(&a.ctr->sm_slot[sm], 1u) * (unsigned)a.nsm + sm;
+                    if (j < nf && atomicExch(&a.yclaim[j], ep) != ep) t = (int)j;
+                }
+            }
+            while (t < 0) {
+                const unsigned i = atomicAdd(&a.ctr->tile_ctr[a.which], 1u);
+                if (i >= nf + nb) break;
+                if (i >= nf) t = a.ntiles - 1 - (int)(i - nf);
+                else if (!a.yclaim || atomicExch(&a.yclaim[i], ep) != ep) t = (int)i;
+            }
         } else {
             const unsigned i = atomicAdd(&a.ctr->tile_ctr[a.which], 1u);
-            if (a.ntiles_dev) {
-                // adaptive y tiles: long jobs from the front, then short ones
-                // from the back of the list
-                const unsigned nf = a.ntiles_dev[0], nb = a.ntiles_dev[1];
-                t = (i < nf) ? (int)i : (i < nf + nb) ? a.ntiles - 1 - (int)(i - nf) : -1;
-            } else {
-                t = (i < (unsigned)a.ntiles) ? (int)i : -1;
-            }
+            t = (i < (unsigned)a.ntiles) ? (int)i : -1;
         }
     }
     return __shfl_sync(0xffffffffu, t, 0);
@@ -445,9 +465,13 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
     constexpr bool kRecord = (VAR == VAR_F64);
     unsigned kbad = 0, nfb = 0;
     bool aborted = false;
+    // step count of this sweep: the claim word of the adaptive tiles
+    const unsigned long long ep = a.yclaim ? __ldcg(&a.ctr->steps) : 0ull;
+    bool first = true;
 
     for (;;) {
-        const int t = claim_tile<T, VAR>(a, lane);
+        const int t = claim_tile<T, VAR>(a, lane, first, ep);
+        first = false;
         if (t < 0) break;
         unsigned tcost = 0;  // estimated work of the tile (solve_work units)
         const Tile tile = a.tiles[t];
@@ -511,6 +535,32 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                 w.w1 = cons_to_prim(K, u, w.ir1);
                 run = (Shortcuts<T>::stencil && same_bits(w.u1, w.u0)) ? 2 : 1;
                 j0 = 2;
+            } else if (Shortcuts<T>::stencil && kc + C - 1 <= klast && kc + C - 1 < n) {
+                // the previous row was a copy, so the window is the fixed
+                // point of a uniform column (u0 = u1, w0 = w1 = wr0, flux
+                // flo): if the chunk's four cells equal u1 bit for bit, the
+                // per-position steps below would copy u0 to rows kc-2 ..
+                // kc+1, leave the window as it is and count no status or
+                // speed -- do exactly that, for the whole warp at once
+                unsigned long long dif = 0;
+#pragma unroll
+                for (int j = 0; j < C; ++j) dif |= (unsigned long long)diff_bits(chunk_cell<T>(sp, j, lane), w.u1);
+                if (__all_sync(0xffffffffu, !valid || (copied && dif == 0))) {
+                    if (valid) {
+                        const Cons<T> out = w.u0;
+#pragma unroll
+                        for (int j = 0; j < C; ++j) {
+                            const unsigned o = (unsigned)(kc + j - 2) * pitch;
+                            q0[o] = out.r;
+                            qn[o] = out.mn;
+                            qt[o] = out.mt;
+                            qe[o] = out.E;
+                        }
+                    }
+                    run += C;
+                    if (kRecord) tcost += C * kUniformWork;
+                    j0 = C;
+                }
             }
             // one copy of the per-cell arithmetic: position k completes the
             // trace of cell k-1, the flux at (k-1)-1/2 and (from k = s0+2 on)
