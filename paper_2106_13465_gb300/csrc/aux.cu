@@ -99,13 +99,19 @@ __device__ __forceinline__ unsigned warp_exclusive_scan(unsigned v, int lane, un
 
 __global__ void retile_y_kernel(const GridDesc* __restrict__ grids, const Tile* __restrict__ stat, int nstat,
                                 const float* __restrict__ ycost, DevCounters* ctr, Tile* __restrict__ tiles,
-                                int cap_tiles, double cap_per_total, double big_per_total) {
+                                int cap_tiles, double cap_per_total, double big_per_total,
+                                double big_of_max) {
     const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int lane = threadIdx.x & 31;
     const unsigned par = (unsigned)(ctr->steps & 1ull);
-    if (i == 0) ctr->ycost_total[par] = 0ull;
     const double total = (double)ctr->ycost_total[par ^ 1u];
-    const float cap = (float)(total * cap_per_total), big = (float)(total * big_per_total);
+    const double bmax = big_of_max * (double)ctr->ycost_max[par ^ 1u];
+    if (i == 0) {
+        ctr->ycost_total[par] = 0ull;
+        ctr->ycost_max[par] = 0u;
+    }
+    const float cap = (float)(total * cap_per_total);
+    const float big = (float)fmax(total * big_per_total, bmax);
     Tile st{};
     const float* cst = nullptr;
     unsigned nf = 0, nb = 0;
@@ -130,11 +136,11 @@ __global__ void retile_y_kernel(const GridDesc* __restrict__ grids, const Tile* 
 
 cudaError_t launch_retile_y(const GridDesc* grids, const Tile* stat, int nstat, const float* ycost,
                             DevCounters* ctr, Tile* tiles, int cap_tiles, double cap_per_total,
-                            double big_per_total, cudaStream_t s) {
+                            double big_per_total, double big_of_max, cudaStream_t s) {
     const int threads = 128;
     const int blocks = (nstat + threads - 1) / threads;
     retile_y_kernel<<<blocks, threads, 0, s>>>(grids, stat, nstat, ycost, ctr, tiles, cap_tiles, cap_per_total,
-                                               big_per_total);
+                                               big_per_total, big_of_max);
     return cudaGetLastError();
 }
 

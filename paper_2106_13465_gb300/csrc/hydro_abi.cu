@@ -427,7 +427,7 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
     if (e != cudaSuccess) return e;
     if (c->y_adaptive) {
         e = launch_retile_y(c->d_grids, c->d_ystat, c->nystat, c->d_ycost, c->d_ctr, c->d_tiles[DIR_Y],
-                            c->ntiles[DIR_Y], c->y_cap, c->y_cap * (kYBigJob / kYCostCap), s);
+                            c->ntiles[DIR_Y], c->y_cap, c->y_cap * (kYBigJob / kYCostCap), kYBigOfMax, s);
         if (e != cudaSuccess) return e;
     }
     if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;

@@ -32,10 +32,15 @@
 // whose recorded work stays below kYCostCap times the mean work of a static
 // tile.  Uniform work keeps the static tiles; where the Riemann solver works
 // harder the tiles get shorter, so no warp is left with a tile far above the
-// average when the queue runs dry.  Pieces of at least kYBigJob times the
-// mean are queued before the others (longest jobs first, the short ones fill
-// the tail).  The work estimate depends only on the state, so the tiling of
-// a run is reproducible.
+// average when the queue runs dry.  Long pieces are queued before the others
+// (longest jobs first, the short ones fill the tail): those of at least
+// kYBigJob times the mean and kYBigOfMax times the largest piece of the
+// previous y sweep.  Where a few rows hold hard Riemann problems (one-row
+// pieces at several times the mean) only they count as long, so they start
+// at once, spread over the SMs, and do not wait behind the ordinary tiles;
+// where the work is spread evenly the ordinary tiles are the long jobs and
+// the split-off remainders the short ones.  The work estimate depends only
+// on the state, so the tiling of a run is reproducible.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -57,6 +62,7 @@ constexpr int kWarpLines = 32;      // lines per warp tile (one per lane)
 constexpr int kYBlock = 1;          // rows per cost block of the adaptive y tiles
 constexpr double kYCostCap = 1.0;   // adaptive y tile work cap / mean static tile work
 constexpr double kYBigJob = 0.5;    // adaptive y tiles queued first: work / mean static tile work
+constexpr double kYBigOfMax = 0.5;  // ... and work / largest piece of the previous y sweep
 constexpr int kSweepThreads = 128;  // threads per CTA of the sweep kernels
 
 // TMA ring geometry per warp.  x sweep: one slot holds a 64-cell segment of
@@ -116,6 +122,7 @@ struct DevCounters {
                                           // list holds ytiles[0] long jobs from its
                                           // front and ytiles[1] short ones from its back
     unsigned long long ycost_total[2];    // recorded y-sweep work, by step parity
+    unsigned int ycost_max[2];            // largest recorded work of a y tile, by step parity
     unsigned int sm_slot[kMaxSmIds];      // y sweep: warps that have started on each SM
 };
 
@@ -180,11 +187,12 @@ cudaError_t launch_sweep(int dir, int var, const SweepArgs<T>& a, int nctas, cud
 // Cut the adaptive y tiles from the recorded work: each of the nstat tiles
 // of the static tiling `stat` (whole cost blocks) is split where its pieces'
 // work would exceed cap_per_total times the total recorded work of the
-// previous y sweep; pieces of at least big_per_total times that total are
-// queued first, the rest last (list of cap_tiles slots).
+// previous y sweep; pieces of at least big_per_total times that total and
+// big_of_max times the largest tile work it recorded are queued first, the
+// rest last (list of cap_tiles slots).
 cudaError_t launch_retile_y(const GridDesc* grids, const Tile* stat, int nstat, const float* ycost,
                             DevCounters* ctr, Tile* tiles, int cap_tiles, double cap_per_total,
-                            double big_per_total, cudaStream_t s);
+                            double big_per_total, double big_of_max, cudaStream_t s);
 
 cudaError_t launch_step_prologue(GridRun* run, const GridDesc* grids, int ngrids,
                                  DevCounters* ctr, const double* dt_override, double cfl,

@@ -535,7 +535,8 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                 w.w1 = cons_to_prim(K, u, w.ir1);
                 run = (Shortcuts<T>::stencil && same_bits(w.u1, w.u0)) ? 2 : 1;
                 j0 = 2;
-            } else if (Shortcuts<T>::stencil && kc + C - 1 <= klast && kc + C - 1 < n) {
+            } else if (Shortcuts<T>::stencil && kc + C - 1 <= klast && kc + C - 1 < n &&
+                       __all_sync(0xffffffffu, !valid || copied)) {
                 // the previous row was a copy, so the window is the fixed
                 // point of a uniform column (u0 = u1, w0 = w1 = wr0, flux
                 // flo): if the chunk's four cells equal u1 bit for bit, the
@@ -545,7 +546,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                 unsigned long long dif = 0;
 #pragma unroll
                 for (int j = 0; j < C; ++j) dif |= (unsigned long long)diff_bits(chunk_cell<T>(sp, j, lane), w.u1);
-                if (__all_sync(0xffffffffu, !valid || (copied && dif == 0))) {
+                if (__all_sync(0xffffffffu, !valid || dif == 0)) {
                     if (valid) {
                         const Cons<T> out = w.u0;
 #pragma unroll
@@ -647,6 +648,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
             for (int b = b0; b <= b1; ++b) cst[b] = dens;
             const unsigned par = (unsigned)(__ldcg(&a.ctr->steps) & 1ull);
             atomicAdd(&a.ctr->ycost_total[par], (unsigned long long)tcost);
+            atomicMax(&a.ctr->ycost_max[par], tcost);
         }
         finish_tile<T, VAR, WHICH>(a, t, tile.grid, acc, redo && valid, tbad, smax, sbits, kbad, lane);
     }
