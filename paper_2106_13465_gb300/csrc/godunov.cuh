@@ -55,9 +55,13 @@ template <class T> struct Prim { T r, u, v, p; };     // u normal, v tangential
 template <class T> struct Cons { T r, mn, mt, E; };   // (rho, m_n, m_t, E)
 
 // ----------------------------------------------------------------- math --
-// IEEE double operations for T = double.  For T = float the translation
-// unit is built with fast single-precision division, square root and
-// power (approximate hardware instructions); see the build script.
+// T = double: IEEE operations, except division (trcp / tdiv: within 1-2 ulp,
+// a third of the FP64 instructions) and powers (below: within a few ulp).
+// On this GPU every FP64 instruction of a warp occupies its FP64 unit for
+// as long as a fused multiply-add, however few of its lanes are active, so
+// the count of FP64 instructions is the cost.  For T = float the
+// translation unit is built with fast single-precision division, square
+// root and power (approximate hardware instructions); see the build script.
 // FP64 powers through exp2(e log2 x): within a few ulp, and cheaper on the
 // FP64 pipe than the extra-precise pow
 __device__ __forceinline__ double tpow(double x, double e) { return exp2(e * log2(x)); }
@@ -66,6 +70,29 @@ __device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
+// FP64 1/b for a positive normal b with a normal reciprocal, within 1 ulp:
+// the FP32 hardware reciprocal of b's significand (relative error below
+// 2^-22 with its truncation), scaled by b's exponent on the integer pipe and
+// refined by one third-order Newton step, r = r0 (1 + e + e^2) with
+// e = 1 - b r0 (remainder e^3 < 2^-66) -- three FP64 operations where an
+// IEEE division takes about nine.  Any other b: IEEE division.
+__device__ __forceinline__ double trcp(double b) {
+    const unsigned hi = (unsigned)__double2hiint(b), lo = (unsigned)__double2loint(b);
+    const int ex = (int)(hi >> 20);  // with the sign bit: negative b gives ex > 0x7ff
+    const float mf = __uint_as_float(0x3f800000u | ((hi & 0x000fffffu) << 3) | (lo >> 29));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));
+    const unsigned fb = __float_as_uint(rf);  // in (1/2, 1]
+    const int er = (int)(fb >> 23) - 127 - (ex - 1023) + 1023;  // biased exponent of r0
+    if (ex == 0 || ex >= 0x7ff || er <= 0 || er >= 0x7ff) return 1.0 / b;
+    const double r0 = __hiloint2double((int)(((unsigned)er << 20) | ((fb & 0x7fffffu) >> 3)), (int)(fb << 29));
+    const double e = fma(-b, r0, 1.0);
+    return fma(r0, fma(e, e, e), r0);
+}
+__device__ __forceinline__ float trcp(float b) { return 1.0f / b; }
+// a / b through trcp (FP64: within 2 ulp for a positive normal b)
+__device__ __forceinline__ double tdiv(double a, double b) { return a * trcp(b); }
+__device__ __forceinline__ float tdiv(float a, float b) { return a / b; }
 __device__ __forceinline__ double tabs(double x) { return fabs(x); }
 __device__ __forceinline__ float tabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
@@ -135,7 +162,7 @@ template <class T>
 __device__ __forceinline__ Prim<T> cons_to_prim(const Consts<T>& K, const Cons<T>& U, T& ir) {
     Prim<T> W;
     W.r = (U.r < K.rho_floor) ? K.rho_floor : U.r;
-    ir = T(1) / W.r;
+    ir = trcp(W.r);
     W.u = U.mn * ir;
     W.v = U.mt * ir;
     const T q2 = tfma(W.u, W.u, W.v * W.v);
@@ -372,11 +399,11 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
         pressure_fn(K, R, p, fr, ar, br, pzr);
         const T F = fl + fr + du;
         // Newton step / p (F == 0: p is the root, the step is exactly 0)
-        const T g = (F == T(0)) ? T(0) : F / tfma(p, bl + br, al + ar);
+        const T g = (F == T(0)) ? T(0) : tdiv(F, tfma(p, bl + br, al + ar));
         T d = g * p;                                    // the step p - p_new
         T pn = p - d;
         T rel = g;                                      // d / p
-        if (pn < K.pmin) { pn = K.pmin; floored = true; d = p - pn; rel = d / p; }
+        if (pn < K.pmin) { pn = K.pmin; floored = true; d = p - pn; rel = tdiv(d, p); }
         if (tabs(d) <= K.tol * pn) {
             if (d != T(0)) {
                 fl -= tfma(al, rel, bl * d);
@@ -424,7 +451,7 @@ __device__ __forceinline__ Prim<T> sample_side(const Consts<T>& K, const Side<T>
     if (st.p > S.p) {
         const T sk = tfma(-S.c, tsqrt(tfma(K.zs, pr, K.z)), sgn * S.u);   // = sgn * S_K
         if (T(0) <= sk) { W.r = S.r; W.u = S.u; W.p = S.p; }
-        else { W.r = S.r * (pr + K.G6) / tfma(K.G6, pr, T(1)); W.u = st.u; W.p = st.p; }
+        else { W.r = tdiv(S.r * (pr + K.G6), tfma(K.G6, pr, T(1))); W.u = st.u; W.p = st.p; }
     } else {
         const T hk = sgn * S.u - S.c;                              // head
         if (T(0) <= hk) { W.r = S.r; W.u = S.u; W.p = S.p; }
@@ -432,11 +459,11 @@ __device__ __forceinline__ Prim<T> sample_side(const Consts<T>& K, const Side<T>
             if (pz < T(0)) pz = pow_z(K, st.p, S.p, S.ip);
             const T tk = tfma(-S.c, pz, sgn * st.u);               // tail
             if (T(0) > tk) {
-                W.r = one ? S.r : S.r * pr / (pz * pz);
+                W.r = one ? S.r : tdiv(S.r * pr, pz * pz);
                 W.u = st.u; W.p = st.p;
             } else {
                 const T c = K.G5 * tfma(sgn * K.G7, S.u, S.c);
-                const T cc = c / S.c;
+                const T cc = tdiv(c, S.c);
                 W.u = sgn * c;
                 if (K.g75) {  // (c/c_K)^5 and (c/c_K)^7
                     const T c2 = cc * cc, c5 = c2 * c2 * cc;
