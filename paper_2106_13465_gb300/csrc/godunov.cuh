@@ -95,6 +95,21 @@ __device__ __forceinline__ double tdiv(double a, double b) { return a * trcp(b);
 __device__ __forceinline__ float tdiv(float a, float b) { return a / b; }
 __device__ __forceinline__ double tabs(double x) { return fabs(x); }
 __device__ __forceinline__ float tabs(float x) { return fabsf(x); }
+// Comparisons on the integer pipe (an FP64 compare costs an FP64 slot).
+// For a, b >= +0 and not NaN the order of the bit patterns is the order of
+// the values; the callers pass pressures (at least the floor) or their
+// magnitudes, and a NaN there yields a NaN result whichever branch it takes.
+__device__ __forceinline__ bool gt_pos(double a, double b) {
+    return __double_as_longlong(a) > __double_as_longlong(b);
+}
+__device__ __forceinline__ bool gt_pos(float a, float b) { return a > b; }
+__device__ __forceinline__ bool eq_pos(double a, double b) {
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+__device__ __forceinline__ bool eq_pos(float a, float b) { return a == b; }
+// x == +-0 exactly as the IEEE comparison
+__device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool is_zero(float x) { return x == 0.0f; }
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
 
@@ -142,7 +157,7 @@ __device__ __forceinline__ double root7(double x) {
 // and in FP32 (where the power is two hardware approximations), exp2/log2.
 template <class T>
 __device__ __forceinline__ T pow_z(const Consts<T>& K, T p, T pK, T ip) {
-    if (p == pK) return T(1);
+    if (eq_pos(p, pK)) return T(1);
     if constexpr (sizeof(T) == 8) {
         if (K.g75) return root7(p * ip);
         const T x = (p - pK) * ip;
@@ -353,7 +368,7 @@ __device__ __forceinline__ Side<T> make_side(const Consts<T>& K, const Prim<T>& 
 template <class T>
 __device__ __forceinline__ void pressure_fn(const Consts<T>& K, const Side<T>& s, T p,
                                             T& f, T& a, T& b, T& pz) {
-    if (p > s.p) {
+    if (gt_pos(p, s.p)) {
         const T q = trsqrt((p + s.B) * s.iA);
         const T dpk = p - s.p;
         f = dpk * q;
@@ -399,17 +414,17 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
         pressure_fn(K, R, p, fr, ar, br, pzr);
         const T F = fl + fr + du;
         // Newton step / p (F == 0: p is the root, the step is exactly 0)
-        const T g = (F == T(0)) ? T(0) : tdiv(F, tfma(p, bl + br, al + ar));
+        const T g = is_zero(F) ? T(0) : tdiv(F, tfma(p, bl + br, al + ar));
         T d = g * p;                                    // the step p - p_new
         T pn = p - d;
         T rel = g;                                      // d / p
         if (pn < K.pmin) { pn = K.pmin; floored = true; d = p - pn; rel = tdiv(d, p); }
-        if (tabs(d) <= K.tol * pn) {
-            if (d != T(0)) {
+        if (!gt_pos(tabs(d), K.tol * pn)) {
+            if (!is_zero(d)) {
                 fl -= tfma(al, rel, bl * d);
                 fr -= tfma(ar, rel, br * d);
-                if (pzl > T(0)) pzl = tfma(-K.z * pzl, rel, pzl);
-                if (pzr > T(0)) pzr = tfma(-K.z * pzr, rel, pzr);
+                if (positive(pzl)) pzl = tfma(-K.z * pzl, rel, pzl);
+                if (positive(pzr)) pzr = tfma(-K.z * pzr, rel, pzr);
             }
             p = pn;
             conv = true;
