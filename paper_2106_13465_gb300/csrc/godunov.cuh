@@ -107,6 +107,15 @@ __device__ __forceinline__ bool eq_pos(double a, double b) {
     return __double_as_longlong(a) == __double_as_longlong(b);
 }
 __device__ __forceinline__ bool eq_pos(float a, float b) { return a == b; }
+// x < c for a floor c >= +0, exactly as the IEEE comparison: the signed
+// order of the patterns, with a NaN of either sign excluded and -0 < +0
+// false
+__device__ __forceinline__ bool below_floor(double x, double c) {
+    const long long ix = __double_as_longlong(x), ic = __double_as_longlong(c);
+    return ix < ic && (unsigned long long)ix <= 0xfff0000000000000ull &&
+           (ic != 0 || ix != (long long)0x8000000000000000ull);
+}
+__device__ __forceinline__ bool below_floor(float x, float c) { return x < c; }
 // x == +-0 exactly as the IEEE comparison
 __device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
 __device__ __forceinline__ bool is_zero(float x) { return x == 0.0f; }
@@ -176,14 +185,14 @@ __device__ __forceinline__ T pow_z(const Consts<T>& K, T p, T pK, T ip) {
 template <class T>
 __device__ __forceinline__ Prim<T> cons_to_prim(const Consts<T>& K, const Cons<T>& U, T& ir) {
     Prim<T> W;
-    W.r = (U.r < K.rho_floor) ? K.rho_floor : U.r;
+    W.r = below_floor(U.r, K.rho_floor) ? K.rho_floor : U.r;
     ir = trcp(W.r);
     W.u = U.mn * ir;
     W.v = U.mt * ir;
     const T q2 = tfma(W.u, W.u, W.v * W.v);
     T p = K.gm1 * tfma(T(-0.5) * W.r, q2, U.E);
     const T pm = W.r * K.cf2g;
-    W.p = (p < pm) ? pm : p;
+    W.p = below_floor(p, pm) ? pm : p;
     return W;
 }
 
@@ -213,7 +222,10 @@ __device__ __forceinline__ T cfl_speed(const Consts<T>& K, const Cons<T>& U) {
 __device__ __forceinline__ double minmod(double a, double b) {
     const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
     const bool take = ((ia ^ ib) >= 0) && ((ia << 1) != 0) && ((ib << 1) != 0);
-    const long long m = __double_as_longlong(fmin(fabs(a), fabs(b))) | (ia & (long long)0x8000000000000000ull);
+    // fmin of the magnitudes on the bit patterns (a NaN loses, as in fmin)
+    const unsigned long long ma = (unsigned long long)ia & 0x7fffffffffffffffull;
+    const unsigned long long mb = (unsigned long long)ib & 0x7fffffffffffffffull;
+    const long long m = (long long)(ma < mb ? ma : mb) | (ia & (long long)0x8000000000000000ull);
     return take ? __longlong_as_double(m) : 0.0;
 }
 // FP32: the sign test through the product (0 when it underflows, i.e. both
@@ -309,11 +321,11 @@ __device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) *
     WR.u = tfma(T(0.5), Du, W0.u) + du;
     WR.v = tfma(T(0.5), Dv, W0.v) + dv;
     WR.p = tfma(T(0.5), Dp, W0.p) + dp;
-    WL.r = (WL.r < K.rho_floor) ? K.rho_floor : WL.r;
-    WR.r = (WR.r < K.rho_floor) ? K.rho_floor : WR.r;
+    WL.r = below_floor(WL.r, K.rho_floor) ? K.rho_floor : WL.r;
+    WR.r = below_floor(WR.r, K.rho_floor) ? K.rho_floor : WR.r;
     const T pml = WL.r * K.cf2g, pmr = WR.r * K.cf2g;
-    WL.p = (WL.p < pml) ? pml : WL.p;
-    WR.p = (WR.p < pmr) ? pmr : WR.p;
+    WL.p = below_floor(WL.p, pml) ? pml : WL.p;
+    WR.p = below_floor(WR.p, pmr) ? pmr : WR.p;
 }
 
 // ------------------------------------------------------ Riemann solver --
