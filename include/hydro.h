@@ -101,7 +101,8 @@ typedef struct {
  * work (Newton iterations, powers, copies of uniform rows) spent on each row
  * of each 32-column group, and before the next y sweep the library splits each
  * model tile into pieces whose recorded work stays below the mean work
- * of a model tile (pieces of at least half that work are queued first), so
+ * of a model tile (pieces reaching half that work and half the largest
+ * piece of the previous y sweep are queued first, spread over the SMs), so
  * regions where the Riemann solver works harder get shorter tiles.  The
  * tiling follows the state, not the timing.  Results
  * are bit-identical for every admissible setting (a cell's update does not
