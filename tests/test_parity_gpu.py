@@ -88,6 +88,32 @@ def test_random_modes_256_periodic_fp64():
     assert rel_err(got, want) <= TOL64
 
 
+def _sonic_rarefaction_tube(gamma, nx=256, ny=4):
+    """Left (1, 0.75, 1) | right (0.125, 0, 0.1) along x, transmissive: a
+    left rarefaction that spans x/t = 0, so interfaces sample inside the fan."""
+    left = np.arange(nx) < nx // 2
+    rho = np.broadcast_to(np.where(left, 1.0, 0.125)[None, :], (ny, nx))
+    u = np.broadcast_to(np.where(left, 0.75, 0.0)[None, :], (ny, nx))
+    p = np.broadcast_to(np.where(left, 1.0, 0.1)[None, :], (ny, nx))
+    U = pr.conserved(rho, u, 0.0, p, gamma)
+    return pr.Problem("sonic", U, pr.mesh_h(nx, ny), (T_,) * 4)
+
+
+@pytest.mark.parametrize("gamma", [5.0 / 3.0, 1.3])
+def test_other_gamma_matches_oracle(gamma):
+    # g = 7/5 takes (p/p_K)^(1/7) as a 7th root and the fan powers 5 and 7 as
+    # products; any other g takes exp2/log2 (and the binomial series near p_K)
+    cases = [pr.sedov(96, gamma=gamma), pr.random_modes(128, gamma=gamma), _sonic_rarefaction_tube(gamma)]
+    for pb in cases:
+        want, wdts, _ = O.run(pb.U, pb.h, pb.bc, 10, P=O.params(gamma=gamma))
+        with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=64, gamma=gamma) as c:
+            c.set_state(0, pb.U)
+            dts = c.step(10, record_dt=True)
+            got = c.get_state(0)
+        assert rel_err(got, want) <= TOL64, pb.name
+        np.testing.assert_allclose(dts[:, 0], wdts, rtol=1e-12)
+
+
 @pytest.mark.parametrize("nx,ny,bc,tile", [
     (37, 53, (P_, P_, R_, R_), 16),
     (53, 37, (T_, T_, P_, P_), 8),
