@@ -77,11 +77,38 @@ SWEEP_SOURCES = ("godunov.cuh", "kernels.h", "sweep_tma.cuh", "sweep_f64.cu", "s
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments and with whitespace runs collapsed
+    (string and character literals kept as written), so that an edit of the
+    comments alone does not change kernel_source_hash."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sweep kernels' sources, comments and layout aside."""
     h = hashlib.sha256()
     for f in SWEEP_SOURCES:
-        with open(os.path.join(ROOT, "paper_2106_13465_gb300", "csrc", f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(ROOT, "paper_2106_13465_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(f.encode() + strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

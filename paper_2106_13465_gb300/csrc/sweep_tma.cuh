@@ -282,10 +282,10 @@ __device__ __forceinline__ float cfl_estimate(const Consts<double>& K, double r,
 // second pass takes the tiles the main pass queued.  -1 when none is left.
 //
 // Adaptive y tiles (FP64): long jobs from the front of the list, then short
-// ones from its back.  The long jobs are the few heavy Riemann problems of a
-// sweep, and two of them on one SM share its FP64 pipe, so a warp's first
-// claim spreads them: the s-th warp to start on SM m takes long job
-// s * nsm + m, if nobody has.  Every long job also stays in the counter's
+// ones from its back.  The long jobs are the few rows of heavy Riemann
+// problems of a sweep, and two of them in one SM sub-partition halve each
+// other's FP64 rate, so a warp's first claim spreads them over the SMs: the
+// s-th warp to start on SM m takes long job s * nsm + m, if nobody has.  Every long job also stays in the counter's
 // order, and a job is taken by whoever first swaps the step count `ep` into
 // its claim word, so each is taken exactly once however many warps an SM
 // runs.
