@@ -131,9 +131,10 @@ typedef struct {
     long long kernel_launches;
 } hydro_stats;
 
-/* Create a context: validates params, allocates two state buffers (the step
- * ping-pongs between them) for all grids plus the per-grid dt/time records,
- * and builds the tile work-lists.  The state is zero until hydro_set_state.
+/* Create a context (the "2D grid buffer for conservative variables" of
+ * Fig. 5 and the scheme parameters of §1): validates params, allocates two
+ * state buffers (the step ping-pongs between them) for all grids plus the
+ * per-grid dt/time records, and builds the tile work-lists.  The state is zero until hydro_set_state.
  * Returns HYDRO_EINVAL for invalid params, HYDRO_ECUDA when no usable GPU is
  * present, HYDRO_ENOMEM when allocation fails; *out is NULL on failure. */
 hydro_status hydro_init(const hydro_params *params, hydro_ctx **out);
@@ -141,9 +142,24 @@ hydro_status hydro_init(const hydro_params *params, hydro_ctx **out);
 /* Release the context and all its device memory.  NULL is a no-op. */
 void hydro_destroy(hydro_ctx *ctx);
 
-/* Choose the launch shape (see hydro_tuning).  HYDRO_EINVAL for values out
- * of range.  Applies to later hydro_step calls. */
+/* Choose the launch shape (see hydro_tuning).  The paper's counterpart is
+ * the choice of domain sizes and task granularity of its CPU versions
+ * (§3-§6); here it only changes the schedule, never a result.  HYDRO_EINVAL
+ * for values out of range.  Applies to later hydro_step calls. */
 hydro_status hydro_set_tuning(hydro_ctx *ctx, const hydro_tuning *tuning);
+
+/* Failure detection (the paper has no counterpart; its MPI/OpenMP runs have
+ * no bounded waits).  Every wait of a sweep warp for a TMA copy into shared
+ * memory gives up after `polls` polls of its mbarrier; the warp then records
+ * the timeout, waits for its own copies still in flight (at most the default
+ * number of polls each) and leaves the kernel, and the hydro_step call that
+ * launched it returns HYDRO_ETIMEOUT.  The state is then undefined until the
+ * next hydro_set_state; the context stays usable.  polls < 0 restores the
+ * default (2^22, far above any real copy's latency).  A small value exists
+ * to exercise this path: polls = 0 makes every sweep give up at its first
+ * wait.  HYDRO_EINVAL for polls >= 2^32.  Synchronises the context's stream;
+ * applies to later hydro_step calls. */
+hydro_status hydro_set_wait_limit(hydro_ctx *ctx, long long polls);
 
 /* Load the state of grid `grid` from U (host or device, [4][ny][nx] FP64).
  * Resets the grid's time to 0 and the context's step counter (which sets the
@@ -224,14 +240,16 @@ hydro_status hydro_conservation(hydro_ctx *ctx, int grid, double sums[4]);
 hydro_status hydro_conservation_noalloc(const double *U, int nx, int ny, double h, double *sums,
                                         void *cuda_stream);
 
-/* Device counters (see hydro_stats). */
+/* Device counters (see hydro_stats): the run's bookkeeping, which the
+ * paper's timings of whole runs (§7) leave to the host. */
 hydro_status hydro_get_stats(hydro_ctx *ctx, hydro_stats *out);
 
 /* Message of the last failure on this context ("" if none); valid until the
- * next call on ctx.  With ctx == NULL: the last hydro_init failure. */
+ * next call on ctx.  With ctx == NULL: the last hydro_init failure.  (Error
+ * reporting of the ABI; the paper has no counterpart.) */
 const char *hydro_last_error(const hydro_ctx *ctx);
 
-/* Library version, "major.minor.patch". */
+/* Library version, "major.minor.patch" (the paper has no counterpart). */
 const char *hydro_version(void);
 
 #ifdef __cplusplus

@@ -28,8 +28,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hydro_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 BC_REFLECT, BC_TRANSMISSIVE, BC_PERIODIC = 0, 1, 2
 
@@ -48,21 +50,46 @@ def params(gamma=1.4, cfl=0.8, niter=10, rho_floor=1e-10, c_floor=1e-10) -> Para
     return Params(gamma, cfl, niter, rho_floor, c_floor)
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so next to the source (gcc, -ffp-contract=off)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile liboracle.so next to the source (gcc, -ffp-contract=off); with
+    omp=True the same source with -fopenmp into liboracle_omp.so (lines of a
+    sweep shared among threads, bit-identical results)."""
+    out = _LIB_OMP if omp else _LIB
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-            tmp = _LIB + f".tmp{os.getpid()}"
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+            tmp = out + f".tmp{os.getpid()}"
             cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-                   "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+                   "-fPIC", "-shared", *(["-fopenmp"] if omp else []), "-o", tmp, _SRC, "-lm"]
             subprocess.run(cmd, check=True)
-            os.replace(tmp, _LIB)
-    return _LIB
+            os.replace(tmp, out)
+    return out
 
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
 _P = ctypes.POINTER(Params)
+
+
+def _bind(L):
+    L.orc_riemann_star.argtypes = [_P, _D, _D, _D, _D]
+    L.orc_sample.argtypes = [_P, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]
+    L.orc_interface_flux.argtypes = [_P, _D, _D, _D]
+    L.orc_run.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _I, _D,
+                          ctypes.c_long, ctypes.c_int, _D, _D]
+    L.orc_run.restype = ctypes.c_int
+    L.orc_sweep.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _I, _D,
+                            ctypes.c_int, ctypes.c_double]
+    L.orc_sweep.restype = ctypes.c_int
+    L.orc_cfl_dt.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
+    L.orc_cfl_dt.restype = ctypes.c_double
+    L.orc_conservation.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
+    L.orc_godunov_line.argtypes = [_P, ctypes.c_int, ctypes.c_double, _D, _D]
+    L.orc_godunov_line.restype = ctypes.c_int
+    L.orc_trace.argtypes = [_P, ctypes.c_double, _D, _D, _D, _D, _D]
+    L.orc_cons_to_prim.argtypes = [_P, _D, _D]
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_set_threads.restype = ctypes.c_int
+    return L
 
 
 def lib():
@@ -73,25 +100,23 @@ def lib():
         path = os.environ.get("ORACLE_LIB")
         if not path:
             path = build()
-        L = ctypes.CDLL(path)
-        L.orc_riemann_star.argtypes = [_P, _D, _D, _D, _D]
-        L.orc_sample.argtypes = [_P, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]
-        L.orc_interface_flux.argtypes = [_P, _D, _D, _D]
-        L.orc_run.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _I, _D,
-                              ctypes.c_long, ctypes.c_int, _D, _D]
-        L.orc_run.restype = ctypes.c_int
-        L.orc_sweep.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _I, _D,
-                                ctypes.c_int, ctypes.c_double]
-        L.orc_sweep.restype = ctypes.c_int
-        L.orc_cfl_dt.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
-        L.orc_cfl_dt.restype = ctypes.c_double
-        L.orc_conservation.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
-        L.orc_godunov_line.argtypes = [_P, ctypes.c_int, ctypes.c_double, _D, _D]
-        L.orc_godunov_line.restype = ctypes.c_int
-        L.orc_trace.argtypes = [_P, ctypes.c_double, _D, _D, _D, _D, _D]
-        L.orc_cons_to_prim.argtypes = [_P, _D, _D]
-        _lib = L
+        _lib = _bind(ctypes.CDLL(path))
     return _lib
+
+
+def lib_omp():
+    """The -fopenmp build of the same source (lines of a sweep shared among
+    threads; bit-identical to lib())."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = _bind(ctypes.CDLL(build(omp=True)))
+    return _lib_omp
+
+
+def set_threads(n: int) -> int:
+    """Threads of the OpenMP build's sweeps (0: its default); returns the
+    number it will use."""
+    return int(lib_omp().orc_set_threads(int(n)))
 
 
 def _dp(a: np.ndarray):
@@ -162,9 +187,15 @@ def _bc(bc) -> ctypes.Array:
 
 
 def run(U: np.ndarray, h: float, bc, nsteps: int, step0: int = 0, dt_override=None,
-        P: Params | None = None, check: bool = True):
-    """Advance a copy of U ([4, ny, nx] FP64) by nsteps; returns (U_new, dts, rc)."""
+        P: Params | None = None, check: bool = True, threads: int | None = None):
+    """Advance a copy of U ([4, ny, nx] FP64) by nsteps; returns (U_new, dts, rc).
+    threads: None runs the single-threaded build; n >= 0 the OpenMP build
+    with n threads (0: its default), which gives the same bits."""
     P = P or params()
+    L = lib()
+    if threads is not None:
+        L = lib_omp()
+        L.orc_set_threads(int(threads))
     a = np.array(U, dtype=np.float64, order="C", copy=True)
     _, ny, nx = a.shape
     dts = np.zeros(max(nsteps, 1))
@@ -173,7 +204,7 @@ def run(U: np.ndarray, h: float, bc, nsteps: int, step0: int = 0, dt_override=No
         ov = np.ascontiguousarray(dt_override, dtype=np.float64)
         if ov.shape[0] < nsteps:
             raise ValueError("dt_override shorter than nsteps")
-    rc = lib().orc_run(ctypes.byref(P), nx, ny, h, _bc(bc), _dp(a), step0, nsteps,
+    rc = L.orc_run(ctypes.byref(P), nx, ny, h, _bc(bc), _dp(a), step0, nsteps,
                        _dp(ov) if ov is not None else None, _dp(dts))
     if check and rc not in (0,):
         raise RuntimeError(f"orc_run failed: {rc}")

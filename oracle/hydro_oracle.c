@@ -33,11 +33,16 @@
  * U[4][ny][nx] in the order (rho, rho*u, rho*v, E), x fastest, FP64.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared hydro_oracle.c -lm
- * (no FMA contraction, so x86 and Arm hosts give the same bits).
+ * (no FMA contraction, so x86 and Arm hosts give the same bits); the same
+ * source with -fopenmp shares the lines of each sweep among threads, with
+ * bit-identical results (see sweep()).
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     double gamma;      /* ratio of specific heats */
@@ -402,7 +407,14 @@ static void apply_bc(grid_t *g, const int bc[4], int dir)
 
 /* One 1D Godunov sweep along dir (0 = x: rows, 1 = y: columns), Fig. 5:
  * boundary conditions, then READ / COMPUTE / WRITE line by line.  The x
- * sweep's normal momentum is rho*u, the y sweep's is rho*v. */
+ * sweep's normal momentum is rho*u, the y sweep's is rho*v.
+ *
+ * Lines are independent (a line reads only its own cells and ghosts and
+ * writes only its own interior cells), so a build with -fopenmp shares the
+ * lines of a sweep among threads, each with its own line buffers, as the
+ * paper's Fine-Grain version shares the loop over lines (§2); every line is
+ * computed by the same code either way, so the results are bit-identical to
+ * the single-threaded build. */
 static int sweep(const orc_params *P, grid_t *g, const int bc[4], int dir,
                  double dtdx)
 {
@@ -410,33 +422,42 @@ static int sweep(const orc_params *P, grid_t *g, const int bc[4], int dir,
     int n = dir == 0 ? g->nx : g->ny;
     int nlines = dir == 0 ? g->ny : g->nx;
     int qn = dir == 0 ? 1 : 2, qt = dir == 0 ? 2 : 1;
-    double (*line)[4] = malloc(sizeof(double[4]) * (size_t)(n + 4));
-    double (*out)[4] = malloc(sizeof(double[4]) * (size_t)n);
-    if (!line || !out) { free(line); free(out); return ORC_ENOMEM; }
-
     int rc = ORC_OK;
-    for (int l = 0; l < nlines && rc == ORC_OK; l++) {
-        /* READ */
-        for (int k = -2; k < n + 2; k++) {
-            int i = dir == 0 ? k : l, j = dir == 0 ? l : k;
-            line[k + 2][0] = *gat(g, 0, i, j);
-            line[k + 2][1] = *gat(g, qn, i, j);
-            line[k + 2][2] = *gat(g, qt, i, j);
-            line[k + 2][3] = *gat(g, 3, i, j);
+
+#ifdef _OPENMP
+#pragma omp parallel reduction(|:rc)
+#endif
+    {
+        double (*line)[4] = malloc(sizeof(double[4]) * (size_t)(n + 4));
+        double (*out)[4] = malloc(sizeof(double[4]) * (size_t)n);
+        if (!line || !out) rc |= ORC_ENOMEM;
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int l = 0; l < nlines; l++) {
+            if (!line || !out || rc != ORC_OK) continue;
+            /* READ */
+            for (int k = -2; k < n + 2; k++) {
+                int i = dir == 0 ? k : l, j = dir == 0 ? l : k;
+                line[k + 2][0] = *gat(g, 0, i, j);
+                line[k + 2][1] = *gat(g, qn, i, j);
+                line[k + 2][2] = *gat(g, qt, i, j);
+                line[k + 2][3] = *gat(g, 3, i, j);
+            }
+            /* COMPUTE */
+            rc |= godunov_line(P, n, dtdx, (const double (*)[4])line, out);
+            /* WRITE */
+            for (int k = 0; k < n; k++) {
+                int i = dir == 0 ? k : l, j = dir == 0 ? l : k;
+                *gat(g, 0, i, j) = out[k][0];
+                *gat(g, qn, i, j) = out[k][1];
+                *gat(g, qt, i, j) = out[k][2];
+                *gat(g, 3, i, j) = out[k][3];
+            }
         }
-        /* COMPUTE */
-        rc = godunov_line(P, n, dtdx, (const double (*)[4])line, out);
-        /* WRITE */
-        for (int k = 0; k < n; k++) {
-            int i = dir == 0 ? k : l, j = dir == 0 ? l : k;
-            *gat(g, 0, i, j) = out[k][0];
-            *gat(g, qn, i, j) = out[k][1];
-            *gat(g, qt, i, j) = out[k][2];
-            *gat(g, 3, i, j) = out[k][3];
-        }
+        free(line);
+        free(out);
     }
-    free(line);
-    free(out);
     return rc;
 }
 
@@ -592,4 +613,17 @@ void orc_trace(const orc_params *P, double dtdx, const double Wm[4],
 void orc_cons_to_prim(const orc_params *P, const double U[4], double W[4])
 {
     cons_to_prim(P, U, W);
+}
+
+/* Threads of the -fopenmp build (0: the OpenMP default); returns the number
+ * of threads a sweep will use, 1 in the single-threaded build. */
+int orc_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
 }

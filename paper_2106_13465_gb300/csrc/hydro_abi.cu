@@ -115,6 +115,7 @@ struct hydro_ctx {
     int tile_len_used[2] = {0, 0};
     long long step = 0;         // steps since the last hydro_set_state
     long long launches = 0;     // kernels launched by the step calls since hydro_init
+    unsigned wait_limit = kWaitLimit;  // polls of a TMA completion before a sweep warp gives up
     cudaGraphExec_t gexec = nullptr;
     int gexec_steps = 0;
     std::string err;
@@ -405,6 +406,7 @@ SweepArgs<T> sweep_args(hydro_ctx* c, int which, const Consts<T>& K) {
     a.nsm = c->nsm;
     a.ycost = c->d_ycost;
     a.tile_smax = c->d_tile_smax;
+    a.wait_limit = c->wait_limit;
     a.which = which;
     a.src_buf = which;
     a.redo_list = c->d_redo;
@@ -658,6 +660,15 @@ hydro_status hydro_set_tuning(hydro_ctx* c, const hydro_tuning* t) {
     c->tuning = n;
     drop_graph(c);
     return upload_tiles(c);
+}
+
+hydro_status hydro_set_wait_limit(hydro_ctx* c, long long polls) {
+    if (!c) return fail(nullptr, HYDRO_EINVAL, "ctx is NULL");
+    if (polls > 0xffffffffLL) return fail(c, HYDRO_EINVAL, "polls must be below 2^32");
+    HCK(c, cudaStreamSynchronize(c->stream));
+    c->wait_limit = polls < 0 ? kWaitLimit : (unsigned)polls;
+    drop_graph(c);  // the captured launches hold the previous limit
+    return HYDRO_OK;
 }
 
 hydro_status hydro_set_state(hydro_ctx* c, int grid, const double* U, int on_device) {

@@ -64,6 +64,10 @@ constexpr double kYCostCap = 1.0;   // adaptive y tile work cap / mean static ti
 constexpr double kYBigJob = 0.5;    // adaptive y tiles queued first: work / mean static tile work
 constexpr double kYBigOfMax = 0.5;  // ... and work / largest piece of the previous y sweep
 constexpr int kSweepThreads = 128;  // threads per CTA of the sweep kernels
+// polls of an mbarrier before a sweep warp gives up waiting for a TMA copy
+// (the default of SweepArgs::wait_limit, and the bound of the wait for the
+// copies still in flight after a timeout)
+constexpr unsigned kWaitLimit = 1u << 22;
 
 // TMA ring geometry per warp.  x sweep: one slot holds a 64-cell segment of
 // one row, 4 planes; y sweep: one slot holds 4 rows x 32 columns, 4 planes.
@@ -142,6 +146,7 @@ struct SweepArgs {
     int nsm;                         // SMs of the device
     float* ycost;                    // y sweep: per-block work recorded here
     unsigned int* tile_smax;         // FP64 second sweep: max FP32 speed estimate per tile
+    unsigned wait_limit;  // polls of a TMA completion before a warp gives up
     int which;       // 0: first sweep of the step, 1: second (folds in CFL max)
     int src_buf;     // buffer index of src (its tensor maps)
     int* redo_list;  // [2][redo_cap] tile indices for the FP32 second pass

@@ -1,5 +1,8 @@
-// sweep_f64.cu -- FP64 instantiation of the fused sweep kernel (IEEE double
-// division, square root and power throughout).
+// sweep_f64.cu -- FP64 instantiation of the fused sweep kernel, and the FP64
+// CFL passes.  FP64 additions, multiplications, fused multiply-adds and
+// square roots are IEEE; divisions go through a refined FP32 reciprocal and
+// the rarefaction power through a 7th root (gamma = 7/5) or exp2/log2, each
+// within a few ulp (godunov.cuh: trcp, root7, pow_z).
 #include "sweep_tma.cuh"
 
 namespace hydro {

@@ -32,15 +32,14 @@
 // walker's register window; wrap-around cells with a direct load.  TMA reads
 // outside the grid are zero-filled and feed no result.
 //
-// Every wait on an mbarrier is bounded: after kWaitLimit polls the warp
-// records STATUS_TIMEOUT, waits (bounded again) for its own copies still in
-// flight and leaves the kernel.
+// Every wait on an mbarrier is bounded: after SweepArgs::wait_limit polls
+// (kWaitLimit unless a caller lowered it to exercise this path) the warp
+// records STATUS_TIMEOUT, waits -- bounded by kWaitLimit -- for its own copies
+// still in flight and leaves the kernel.
 #pragma once
 #include "kernels.h"
 
 namespace hydro {
-
-constexpr unsigned kWaitLimit = 1u << 22;
 
 // --------------------------------------------------------------- PTX ------
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -67,8 +66,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-    for (unsigned it = 0; it < kWaitLimit; ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit = kWaitLimit) {
+    for (unsigned it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -226,16 +225,18 @@ struct WarpRing {
         tma_load_3d(base + s * SLOT, map, x, y, 0, &bar[s]);
         pending |= 1u << s;
     }
-    // all lanes: wait for slot s (bounded; the verdict is warp-uniform)
-    __device__ __forceinline__ bool wait(int s, int lane) {
-        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[s], (parity >> s) & 1u));
+    // all lanes: wait for slot s, at most `limit` polls (the verdict is
+    // warp-uniform)
+    __device__ __forceinline__ bool wait(int s, int lane, unsigned limit) {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[s], (parity >> s) & 1u, limit));
         if (ok) {
             parity ^= 1u << s;
             if (lane == 0) pending &= ~(1u << s);
         }
         return ok;
     }
-    // lane 0, after a timeout: wait (bounded) for this warp's copies in flight
+    // lane 0, after a timeout: wait (at most kWaitLimit polls each) for this
+    // warp's copies in flight
     __device__ __forceinline__ void drain() {
         for (int s = 0; s < S; ++s)
             if (pending & (1u << s)) mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
@@ -518,7 +519,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
 
         for (int c = 0; c < nch; ++c) {
             const int sl = c % S;
-            if (!ring.wait(sl, lane)) { aborted = true; break; }
+            if (!ring.wait(sl, lane, a.wait_limit)) { aborted = true; break; }
             const T* sp = reinterpret_cast<const T*>(ring.slot(sl));
             const int kc = kfirst + c * C;
             int j0 = 0;
@@ -777,7 +778,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
         for (int c = 0; c < nseg; ++c) {
             const int x = -4 + STEP * (k0 + c);
             const int sl = c % S;
-            if (!ring.wait(sl, lane)) { aborted = true; break; }
+            if (!ring.wait(sl, lane, a.wait_limit)) { aborted = true; break; }
             const int A = x + 2 * lane;
             Cons<T> uA, uB;
             read_pair<T>(ring.slot(sl), 2 * lane, uA, uB);

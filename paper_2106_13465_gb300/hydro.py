@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "HYDRO_OK", 1: "HYDRO_EINVAL", 2: "HYDRO_ENOMEM", 3: "HYDRO_E
                 4: "HYDRO_ENEGATIVE", 5: "HYDRO_ETIMEOUT"}
 
 # every symbol the header declares (checked by the CPU test of the ABI)
-EXPORTS = ("hydro_init", "hydro_destroy", "hydro_set_tuning", "hydro_set_state",
+EXPORTS = ("hydro_init", "hydro_destroy", "hydro_set_tuning", "hydro_set_wait_limit", "hydro_set_state",
            "hydro_get_state", "hydro_step", "hydro_step_dt", "hydro_step_profiled", "hydro_cfl_dt", "hydro_get_time",
            "hydro_get_step", "hydro_set_step", "hydro_set_time",
            "hydro_conservation", "hydro_conservation_noalloc", "hydro_get_stats",
@@ -78,6 +78,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.hydro_destroy.argtypes = [vp]
     L.hydro_destroy.restype = None
     L.hydro_set_tuning.argtypes = [vp, P(hydro_tuning)]
+    L.hydro_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     L.hydro_set_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
     L.hydro_get_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
     L.hydro_step.argtypes = [vp, ctypes.c_int, D]
@@ -96,7 +97,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.hydro_last_error.restype = ctypes.c_char_p
     L.hydro_version.argtypes = []
     L.hydro_version.restype = ctypes.c_char_p
-    for name in ("hydro_init", "hydro_set_tuning", "hydro_set_state", "hydro_get_state",
+    for name in ("hydro_init", "hydro_set_tuning", "hydro_set_wait_limit", "hydro_set_state", "hydro_get_state",
                  "hydro_step", "hydro_step_dt", "hydro_step_profiled", "hydro_cfl_dt",
                  "hydro_get_time", "hydro_get_step", "hydro_set_step", "hydro_set_time",
                  "hydro_conservation", "hydro_get_stats"):
@@ -128,6 +129,10 @@ def hydro_destroy(ctx) -> None:
 
 def hydro_set_tuning(ctx, tuning: hydro_tuning) -> int:
     return load().hydro_set_tuning(ctx, ctypes.byref(tuning))
+
+
+def hydro_set_wait_limit(ctx, polls: int) -> int:
+    return load().hydro_set_wait_limit(ctx, polls)
 
 
 def hydro_set_state(ctx, grid: int, U_ptr: int, on_device: int) -> int:
@@ -253,6 +258,10 @@ class Context:
     def set_tuning(self, tile_len: int = 0, ctas_per_sm: int = 0, graph_steps: int = 20,
                    span_len: int = 0) -> None:
         self._check(hydro_set_tuning(self.ctx, hydro_tuning(tile_len, ctas_per_sm, graph_steps, span_len)))
+
+    def set_wait_limit(self, polls: int = -1) -> None:
+        """Polls of a TMA completion before a sweep gives up (-1: default)."""
+        self._check(hydro_set_wait_limit(self.ctx, polls))
 
     def set_state(self, grid: int, U) -> None:
         if hasattr(U, "data_ptr"):

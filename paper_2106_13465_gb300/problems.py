@@ -130,16 +130,22 @@ def random_modes(nx: int, ny: int | None = None, seed: int = SEED, gamma: float 
     j = np.arange(ny)[rows] if rows is not None else np.arange(ny)
     x = (np.arange(nx) + 0.5) * h
     y = (j + 0.5) * h
-    X, Y = np.meshgrid(x, y)
-    rho = np.ones_like(X)
+    # each mode cos(2 pi (k0 x + k1 y) + phi) = cos(a + b) with a = 2 pi k0 x
+    # and b = 2 pi k1 y + phi, expanded by the angle-sum identities into
+    # outer products of row and column vectors (a band of rows gets the same
+    # values as inside the full field)
+    two_pi = 2.0 * np.pi
+    rho = np.ones((len(j), nx))
     for (k, ph) in zip(kr, phr):
-        rho += 0.1 * np.cos(2.0 * np.pi * (k[0] * X + k[1] * Y) + ph)
-    u = np.zeros_like(X)
-    v = np.zeros_like(X)
+        a, b = two_pi * k[0] * x, two_pi * k[1] * y + ph
+        rho += 0.1 * (np.outer(np.cos(b), np.cos(a)) - np.outer(np.sin(b), np.sin(a)))
+    u = np.zeros_like(rho)
+    v = np.zeros_like(rho)
     for (k, ph) in zip(kv, phv):
-        arg = 2.0 * np.pi * (k[0] * X + k[1] * Y) + ph
-        u += 0.2 * np.cos(arg)
-        v += 0.2 * np.sin(arg)
+        a, b = two_pi * k[0] * x, two_pi * k[1] * y + ph
+        ca, sa, cb, sb = np.cos(a), np.sin(a), np.cos(b), np.sin(b)
+        u += 0.2 * (np.outer(cb, ca) - np.outer(sb, sa))
+        v += 0.2 * (np.outer(cb, sa) + np.outer(sb, ca))
     U = conserved(rho, u, v, 1.0, gamma)
     return Problem(f"modes{nx}x{ny}", U, h, (PERIODIC,) * 4,
                    {"k_rho": kr.tolist(), "k_vel": kv.tolist()})

@@ -48,6 +48,11 @@ MUTANTS = {
                                     "double eint = U[3] - rho * (un * un + ut * ut);"),
     "cfl_sums_speeds": ("double s = ((au > av) ? au : av) + c;", "double s = au + av + c;"),
     "sweep_order_swapped": ("if (((step0 + s) & 1) == 0) {", "if (((step0 + s) & 1) == 1) {"),
+    "pressure_floor_linear_in_c": ("double pmin = rho * P->c_floor * P->c_floor / P->gamma;",
+                                   "double pmin = rho * P->c_floor / P->gamma;"),
+    "density_floor_ignored": ("return (rho < P->rho_floor) ? P->rho_floor : rho;", "return rho;"),
+    "riemann_floor_drops_gamma": ("return P->rho_floor * P->c_floor * P->c_floor / P->gamma;",
+                                  "return P->rho_floor * P->c_floor * P->c_floor;"),
 }
 
 

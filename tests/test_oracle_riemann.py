@@ -198,3 +198,50 @@ def test_interface_flux_of_a_supersonic_state_is_its_physical_flux():
     E = w[3] / (G - 1) + 0.5 * w[0] * (w[1] ** 2 + w[2] ** 2)
     want = [w[0] * w[1], w[0] * w[1] ** 2 + w[3], w[0] * w[1] * w[2], w[1] * (E + w[3])]
     assert np.allclose(f, want, rtol=1e-15, atol=0)
+
+
+# ---- floors (density floor, pressure floor p >= rho c_floor^2 / gamma) -----
+# Floors of 1e-3 (density) and 0.1 (sound speed) with gamma = 1.4: the
+# pressure floor of a state at the density floor is 1e-3 * 0.01 / 1.4.
+_FLOORS = dict(rho_floor=1e-3, c_floor=0.1)
+_PFLOOR = 7.142857142857143e-06
+
+
+def test_floors_clamp_the_primitive_state_to_their_magnitudes():
+    P = O.params(**_FLOORS)
+    # density below its floor, internal energy negative
+    W = O.cons_to_prim([1e-4, 2e-4, -3e-4, 1e-9], P)
+    assert W[0] == 1e-3
+    assert W[1] == pytest.approx(0.2, rel=1e-15) and W[2] == pytest.approx(-0.3, rel=1e-15)
+    assert W[3] == pytest.approx(_PFLOOR, rel=1e-15)
+    # a pressure above the floor of its density is kept
+    W = O.cons_to_prim([2.0, 0.0, 0.0, 1.0], P)
+    assert W[3] == pytest.approx(0.4, rel=1e-15)
+    # at density 0.5 the floor is 0.5 * 0.01 / 1.4
+    W = O.cons_to_prim([0.5, 0.0, 0.0, 1e-12], P)
+    assert W[3] == pytest.approx(0.5 * 0.01 / 1.4, rel=1e-15)
+
+
+def test_trace_faces_clamped_to_the_floors():
+    """A steep density drop swept by a fast inflow: the predictor drives both
+    face densities negative (rho 1 -+ 0.4995 - 2.4975), so both take the
+    density floor and then the pressure floor of that density."""
+    P = O.params(**_FLOORS)
+    wl, wr = O.trace(0.5, [2.0, -10.0, 0.0, 1e-12], [1.0, -10.0, 0.0, 1e-12],
+                     [0.001, -10.0, 0.0, 1e-12], P)
+    for w in (wl, wr):
+        assert w[0] == 1e-3
+        assert w[1] == -10.0 and w[2] == 0.0
+        assert w[3] == pytest.approx(_PFLOOR, rel=1e-15)
+
+
+def test_vacuum_generating_pair_drives_pstar_to_the_floor():
+    """Streams leaving each other faster than 2 (cL + cR)/(gamma - 1) open a
+    vacuum; the iteration is clamped at the smallest admissible pressure,
+    rho_floor c_floor^2 / gamma, and no vacuum state is formed."""
+    P = O.params(**_FLOORS)
+    c = math.sqrt(1.4)
+    assert 20.0 > 2 * (2 * c) / 0.4
+    ps, us = O.riemann_star([1.0, -10.0, 0.0, 1.0], [1.0, 10.0, 0.0, 1.0], P)
+    assert ps == pytest.approx(_PFLOOR, rel=1e-15)
+    assert us == 0.0

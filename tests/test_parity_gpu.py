@@ -39,8 +39,8 @@ def rel_err(a, b, floor_frac=1e-3):
     return worst
 
 
-def gpu_run(pb, nsteps, precision=64, step0=0, dt_override=None, tuning=None, record=True):
-    with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=precision) as c:
+def gpu_run(pb, nsteps, precision=64, step0=0, dt_override=None, tuning=None, record=True, **kw):
+    with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=precision, **kw) as c:
         if tuning:
             c.set_tuning(**tuning)
         c.set_state(0, pb.U)
@@ -363,6 +363,22 @@ def test_fp32_near_vacuum_interfaces_use_fp64():
     got, _, stats = gpu_run(pb, 5, precision=32, dt_override=dts)
     assert stats["riemann_fp64"] > 0
     assert np.abs(got[0] - ref[0]).max() < 1e-4
+
+
+def test_density_and_pressure_floors_active_match_oracle():
+    """Floors well above the state's low values (density 0.05, sound speed
+    0.3): the strong double rarefaction of two separating streams drives the
+    star density and pressure below them, so the conversion, trace and
+    Riemann floors all act.  The GPU matches the oracle run with the same
+    floors, and the floors change the result (they are active)."""
+    pb = _vacuum_pair(64, 6)
+    kw = dict(rho_floor=0.05, c_floor=0.3)
+    want, dts, _ = O.run(pb.U, pb.h, pb.bc, 6, P=O.params(**kw))
+    got, gdts, _ = gpu_run(pb, 6, **kw)
+    assert rel_err(got, want) <= TOL64
+    assert np.allclose(gdts, dts, rtol=1e-12)
+    free, _, _ = O.run(pb.U, pb.h, pb.bc, 6, dt_override=dts)
+    assert rel_err(free, want) > 1e-3
 
 
 def test_nan_state_reported_and_context_stays_usable():
