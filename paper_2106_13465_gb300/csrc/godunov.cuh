@@ -116,6 +116,18 @@ __device__ __forceinline__ bool below_floor(double x, double c) {
            (ic != 0 || ix != (long long)0x8000000000000000ull);
 }
 __device__ __forceinline__ bool below_floor(float x, float c) { return x < c; }
+// 0 <= x and x < 0 exactly as the IEEE comparisons (a NaN is neither), on
+// the bit pattern: the sign bit, with -0 counted as zero
+__device__ __forceinline__ bool ge_zero(double x) {
+    const long long i = __double_as_longlong(x);
+    return i >= 0 ? i <= 0x7ff0000000000000ll : i == (long long)0x8000000000000000ull;
+}
+__device__ __forceinline__ bool ge_zero(float x) { return 0.0f <= x; }
+__device__ __forceinline__ bool lt_zero(double x) {
+    const long long i = __double_as_longlong(x);
+    return i < 0 && i != (long long)0x8000000000000000ull && (unsigned long long)i <= 0xfff0000000000000ull;
+}
+__device__ __forceinline__ bool lt_zero(float x) { return x < 0.0f; }
 // x == +-0 exactly as the IEEE comparison
 __device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
 __device__ __forceinline__ bool is_zero(float x) { return x == 0.0f; }
@@ -406,17 +418,21 @@ struct Star {
 // (p*, u*) by Newton from the PVRS estimate
 //   p0 = (pL+pR)/2 - (uR-uL)(rhoL+rhoR)(cL+cR)/8,
 // every iterate clamped to pmin, at most niter steps.  The iteration stops
-// once a step changes p by no more than tol * p: the iterate is then the
-// root to rounding, and f_K and (p/p_K)^z at the new iterate follow from
-// their values at the previous one by a first-order update (the neglected
-// term is O(tol^2)).  Without convergence f_K is evaluated again at the
-// last iterate.  u* = (uL+uR)/2 + (f_R(p*) - f_L(p*))/2.
+// once a step changes p by no more than tol * p.  Newton's method converges
+// quadratically: after a step of relative size d the error of the new
+// iterate is about (k/2) d^2, where k = p F''/F' is of order one for these
+// pressure functions (at most 1 for the shock branch, 1 - z for the
+// rarefaction branch).  tol = 1e-8 (FP64) and 3e-4 (FP32) therefore leave an
+// error below the type's rounding, and f_K and (p/p_K)^z at the new iterate
+// follow from their values at the previous one by a first-order update (the
+// neglected term is of the same order).  Without convergence f_K is
+// evaluated again at the last iterate.  u* = (uL+uR)/2 + (f_R(p*) - f_L(p*))/2.
 template <class T>
 __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T>& L,
                                                 const Side<T>& R) {
     T p = tfma(T(-0.125) * (R.u - L.u), (L.r + R.r) * (L.c + R.c), T(0.5) * (L.p + R.p));
     bool floored = false;
-    if (p < K.pmin) { p = K.pmin; floored = true; }
+    if (below_floor(p, K.pmin)) { p = K.pmin; floored = true; }
     const T du = R.u - L.u;
     T fl, al, bl, pzl, fr, ar, br, pzr;
     bool conv = false;
@@ -430,7 +446,7 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
         T d = g * p;                                    // the step p - p_new
         T pn = p - d;
         T rel = g;                                      // d / p
-        if (pn < K.pmin) { pn = K.pmin; floored = true; d = p - pn; rel = tdiv(d, p); }
+        if (below_floor(pn, K.pmin)) { pn = K.pmin; floored = true; d = p - pn; rel = tdiv(d, p); }
         if (!gt_pos(tabs(d), K.tol * pn)) {
             if (!is_zero(d)) {
                 fl -= tfma(al, rel, bl * d);
@@ -473,19 +489,19 @@ __device__ __forceinline__ Prim<T> sample_side(const Consts<T>& K, const Side<T>
     // sgn = +1 for the left side, -1 for the right side (mirror formulas)
     Prim<T> W;
     W.v = S.v;
-    const bool one = (st.p == S.p);
+    const bool one = eq_pos(st.p, S.p);
     const T pr = one ? T(1) : st.p * S.ip;
-    if (st.p > S.p) {
+    if (gt_pos(st.p, S.p)) {
         const T sk = tfma(-S.c, tsqrt(tfma(K.zs, pr, K.z)), sgn * S.u);   // = sgn * S_K
-        if (T(0) <= sk) { W.r = S.r; W.u = S.u; W.p = S.p; }
+        if (ge_zero(sk)) { W.r = S.r; W.u = S.u; W.p = S.p; }
         else { W.r = tdiv(S.r * (pr + K.G6), tfma(K.G6, pr, T(1))); W.u = st.u; W.p = st.p; }
     } else {
         const T hk = sgn * S.u - S.c;                              // head
-        if (T(0) <= hk) { W.r = S.r; W.u = S.u; W.p = S.p; }
+        if (ge_zero(hk)) { W.r = S.r; W.u = S.u; W.p = S.p; }
         else {
-            if (pz < T(0)) pz = pow_z(K, st.p, S.p, S.ip);
+            if (lt_zero(pz)) pz = pow_z(K, st.p, S.p, S.ip);
             const T tk = tfma(-S.c, pz, sgn * st.u);               // tail
-            if (T(0) > tk) {
+            if (lt_zero(tk)) {
                 W.r = one ? S.r : tdiv(S.r * pr, pz * pz);
                 W.u = st.u; W.p = st.p;
             } else {
@@ -509,7 +525,7 @@ __device__ __forceinline__ Prim<T> sample_side(const Consts<T>& K, const Side<T>
 template <class T>
 __device__ __forceinline__ Prim<T> sample0(const Consts<T>& K, const Side<T>& L,
                                            const Side<T>& R, const Star<T>& st) {
-    if (T(0) <= st.u) return sample_side(K, L, st.pzl, st, T(1));
+    if (ge_zero(st.u)) return sample_side(K, L, st.pzl, st, T(1));
     return sample_side(K, R, st.pzr, st, T(-1));
 }
 

@@ -546,8 +546,9 @@ hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
     c->prec = params->precision;
     c->esz = c->prec == 64 ? 8 : 4;
     c->cfl = params->cfl;
-    c->Kd = make_consts<double>(*params, 1e-12);
-    c->Kf = make_consts<float>(*params, 1e-6);
+    // Newton convergence tolerances (godunov.cuh: riemann_star)
+    c->Kd = make_consts<double>(*params, 1e-8);
+    c->Kf = make_consts<float>(*params, 3e-4);
     c->grids.assign(params->grids, params->grids + params->ngrids);
     cudaGetDevice(&c->device);
     cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);

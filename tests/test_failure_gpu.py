@@ -23,8 +23,10 @@ TOL64 = 1e-11
 
 
 def _rel(a, b):
+    """Relative error, floored at 1e-3 of the plane's scale for the momenta."""
     scale = np.abs(b).reshape(4, -1).max(axis=1)[:, None, None]
-    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-3 * scale)))
+    floor = np.array([0.0, 1e-3, 1e-3, 0.0])[:, None, None] * scale
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), floor)))
 
 
 @pytest.mark.parametrize("precision", [64, 32])

@@ -1,16 +1,18 @@
 """GPU parity: the CUDA path, called through the C ABI, against the FP64
 oracle on the same seeded inputs.
 
-Tolerance (FP64 path): max over cells and variables of
-    |gpu - oracle| / max(|oracle|, 1e-3 * max_cells |oracle_q|)  <= 1e-11,
-i.e. a relative error, with a floor at 1e-3 of each variable's largest
-magnitude so that values created by cancellation near zero (momentum at a
-wave's leading edge) are judged against the scale that produced them.  The
-two sides differ only in rounding: fused multiply-adds, the library's pow
-and the reciprocal-multiply forms on the GPU, and the Newton early exit
-(which stops once a step moves p* by <= 1e-12 p*, i.e. at the converged
-value).  Integer-like facts (exact zeros, uniform regions, symmetries) are
-checked bit-exactly.
+Tolerance (FP64 path): max over cells of the relative error |gpu - oracle|
+/ |oracle| <= 1e-11 for the density and the total energy (strictly
+positive), and for the two momenta the relative error with a floor at 1e-3
+of the momentum's largest magnitude, |gpu - oracle| / max(|oracle|, 1e-3 *
+max_cells |oracle_q|) <= 1e-11: a momentum passes through zero, and where it
+is created by cancellation (at a wave's leading edge) its absolute rounding
+error is that of the momentum scale that produced it.  The two sides differ
+only in rounding: fused multiply-adds, the reciprocal-multiply forms and the
+powers on the GPU against the C library's division and pow, and the Newton
+early exit (which stops once a step moves p* by <= 1e-8 p*, after which the
+error is below rounding).  Integer-like facts (exact zeros, uniform regions,
+symmetries) are checked bit-exactly.
 """
 import math
 
@@ -25,15 +27,23 @@ pytestmark = pytest.mark.gpu
 
 P_, T_, R_ = pr.PERIODIC, pr.TRANSMISSIVE, pr.REFLECT
 TOL64 = 1e-11
+# FP32 path: relative L1 density error against the FP64 oracle on the same
+# dt sequence, 256^2 random modes after 10 steps (a few times the measured
+# 1.2e-7, so a precision regression of the FP32 arithmetic fails it)
+TOL_L1_FP32 = 5e-7
 
 
 def rel_err(a, b, floor_frac=1e-3):
+    """Worst relative error over cells and variables: unfloored for density
+    and energy (planes 0 and 3), floored at floor_frac of the plane's largest
+    magnitude for the momenta (planes 1 and 2)."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     worst = 0.0
     for q in range(a.shape[0]):
-        scale = np.abs(b[q]).max()
-        den = np.maximum(np.abs(b[q]), floor_frac * scale)
+        den = np.abs(b[q])
+        if q in (1, 2):
+            den = np.maximum(den, floor_frac * den.max())
         den = np.where(den > 0, den, 1.0)
         worst = max(worst, float((np.abs(a[q] - b[q]) / den).max()))
     return worst
@@ -351,7 +361,7 @@ def test_fp32_density_error_against_fp64_with_replayed_dt():
     ref, dts, _ = O.run(pb.U, pb.h, pb.bc, 10)
     got, _, stats = gpu_run(pb, 10, precision=32, dt_override=dts)
     l1 = np.abs(got[0] - ref[0]).sum() / np.abs(ref[0]).sum()
-    assert l1 < 1e-5, l1
+    assert l1 < TOL_L1_FP32, l1
     assert stats["status_flags"] == 0
 
 

@@ -19,14 +19,17 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-11
 # FP32 batch (FP64 dt replayed, 10 steps): relative L1 density error per grid
-TOL_L1_FP32_BATCH = 1e-6
+TOL_L1_FP32_BATCH = 5e-7  # measured 1.3e-7 (worst grid)
 
 
 def rel_err(a, b, floor_frac=1e-3):
+    """Unfloored relative error for density and energy, floored at
+    floor_frac of the plane's largest magnitude for the momenta."""
     worst = 0.0
     for q in range(a.shape[0]):
-        scale = np.abs(b[q]).max()
-        den = np.maximum(np.abs(b[q]), floor_frac * scale)
+        den = np.abs(b[q])
+        if q in (1, 2):
+            den = np.maximum(den, floor_frac * den.max())
         den = np.where(den > 0, den, 1.0)
         worst = max(worst, float((np.abs(a[q] - b[q]) / den).max()))
     return worst
