@@ -89,7 +89,7 @@ def load_peaks() -> dict:
         return {}
 
 
-SWEEP_SOURCES = ("godunov.cuh", "kernels.h", "sweep_tma.cuh", "sweep_f64.cu", "sweep_f32.cu")
+SWEEP_SOURCES = ("godunov.cuh", "kernels.h", "sweep_tma.cuh", "fused_tma.cuh", "sweep_f64.cu", "sweep_f32.cu")
 
 # FP64 pipe of a GB300: 152 SMs x 2 DFMA per clock x 2 flops x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
@@ -324,19 +324,24 @@ def timed_steps(ctx, steps: int, warmup: int, stream, dist, torch, sampler=None)
     par = (kstep0 + np.arange(kp)) % 2  # even steps sweep x first, odd steps y first
     return {"ms": ms, "launches": launches, "clocks": clocks,
             "sweep_ms": float(np.mean(kern[:, 1:])), "prologue_ms": float(np.mean(kern[:, 0])),
+            "step_kernels_ms": float(np.mean(kern[:, 1] + kern[:, 2])),
             "x_ms": float(np.mean(np.where(par == 0, kern[:, 1], kern[:, 2]))),
             "y_ms": float(np.mean(np.where(par == 0, kern[:, 2], kern[:, 1])))}
 
 
-def roofline_for(workload: str, prec: int, cells: int, sweep_ms: float) -> dict:
-    """Roofline of the sweep kernel: HBM view (algorithmic bytes, a read and a
-    write of the 4 planes of every cell per sweep) and, for FP64 with a
-    recorded flop count, the FP64-pipe view; `bound` is the one with the
-    larger fraction.  `traffic`: ncu DRAM bytes per sweep launch recorded on
-    the current kernel sources, else null."""
+def roofline_for(workload: str, prec: int, cells: int, m: dict, fused: bool = False) -> dict:
+    """Roofline of the dominant kernel: the sweep kernel (mean of the x and y
+    launches), or with fused steps the step kernel.  HBM view: algorithmic
+    bytes, a read and a write of the 4 planes of every cell per launch (a
+    sweep, or a whole fused step); FP64 with a recorded flop count also the
+    FP64-pipe view; `bound` is the one with the larger fraction.  `traffic`:
+    ncu DRAM bytes per launch recorded on the current kernel sources, else
+    null."""
     peaks = load_peaks()
-    prof = recorded_profile(workload)
+    key = workload + ("_fused" if fused else "")
+    prof = recorded_profile(key)
     esz = 8 if prec == 64 else 4
+    sweep_ms = m["step_kernels_ms"] if fused else m["sweep_ms"]
     alg_bytes = 2.0 * 4 * esz * cells
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     hbm_achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
@@ -346,7 +351,8 @@ def roofline_for(workload: str, prec: int, cells: int, sweep_ms: float) -> dict:
     flops_cell = prof.get("fp64_flops_per_cell_sweep")
     alu = None
     if prec == 64 and flops_cell:
-        achieved = flops_cell * cells / (sweep_ms * 1e-3) / 1e12
+        # a fused launch does both sweeps of every cell
+        achieved = flops_cell * (2 if fused else 1) * cells / (sweep_ms * 1e-3) / 1e12
         alu = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                "frac": achieved / FP64_PEAK_TFLOPS,
                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)",
@@ -358,8 +364,9 @@ def roofline_for(workload: str, prec: int, cells: int, sweep_ms: float) -> dict:
         if alu:
             roof["alu_view"] = alu
     roof["traffic"] = prof.get("dram_bytes_per_sweep")
-    roof.update({"kernel": "sweep_x_kernel / sweep_y_kernel (mean of both)", "launch_ms": sweep_ms,
-                 "algorithmic_bytes_per_launch": alg_bytes})
+    roof.update({"kernel": ("fused_step_kernel (with its second pass)" if fused
+                            else "sweep_x_kernel / sweep_y_kernel (mean of both)"),
+                 "launch_ms": sweep_ms, "algorithmic_bytes_per_launch": alg_bytes})
     return roof
 
 
@@ -392,6 +399,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     stream = torch.cuda.Stream()
     ctx = H.Context(grids, precision=prec, stream=stream.cuda_stream)
+    if args.fused is not None:
+        tuning = dict(tuning or {}, fused=args.fused)
     if tuning:
         ctx.set_tuning(graph_steps=20, **tuning)
     for g, p in enumerate(pbs):
@@ -438,6 +447,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     precision_report = None
     if companion or (prec == 32 and l1_steps > 0):
         c64 = H.Context(grids, precision=64, stream=stream.cuda_stream)
+        if args.fused is not None:
+            c64.set_tuning(graph_steps=20, fused=args.fused)
         for g, p in enumerate(pbs):
             c64.set_state(g, p.U)
         dts = ref = None
@@ -452,8 +463,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                     "steps": args.steps, "warmup": args.warmup, "gpu_launches": m64["launches"],
                     "start_step": (l1_steps if rank == 0 else 0),
                     "kernels_ms": {"prologue": m64["prologue_ms"], "sweep": m64["sweep_ms"],
+                                   "step_kernels": m64["step_kernels_ms"],
                                    "x_sweep": m64["x_ms"], "y_sweep": m64["y_ms"]},
-                    "roofline": roofline_for(companion, 64, cells, m64["sweep_ms"])}
+                    "roofline": roofline_for(companion, 64, cells, m64, bool(args.fused))}
         c64.close()
         if ref is not None:
             with H.Context(grids, precision=32, stream=stream.cuda_stream) as c32:
@@ -475,7 +487,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             dist.destroy_process_group()
         return
 
-    roofline = roofline_for(primary, prec, cells, m["sweep_ms"])
+    roofline = roofline_for(primary, prec, cells, m, bool(args.fused))
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -506,7 +518,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "e2e": e2e,
         "gpu_launches": m["launches"],
         "clocks": m["clocks"],
-        "kernels_ms": {"prologue": m["prologue_ms"], "sweep": m["sweep_ms"], "x_sweep": m["x_ms"],
+        "kernels_ms": {"prologue": m["prologue_ms"], "sweep": m["sweep_ms"],
+                       "step_kernels": m["step_kernels_ms"], "x_sweep": m["x_ms"],
                        "y_sweep": m["y_ms"]},
         "riemann_fp64_fallbacks": stats["riemann_fp64"],
         "fp64": fp64,
@@ -532,6 +545,9 @@ def main():
                          "steps (default: 200 for the paired workloads, else 0)")
     ap.add_argument("--autotune", action="store_true",
                     help="time candidate launch shapes first and use the fastest")
+    ap.add_argument("--fused", type=int, default=None, choices=[0, 1],
+                    help="1: one fused step kernel per step (both sweeps of a tile in shared memory); "
+                         "0: two sweep kernels; default: the library default (0)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

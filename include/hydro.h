@@ -94,6 +94,14 @@ typedef struct {
  *   span_len      x sweep: results of a row per warp task (a multiple of 60:
  *                 a warp walks a row in overlapping 64-cell segments that
  *                 yield 60 results each)
+ *   fused         0: a step is two sweep launches, one per direction (the
+ *                 state crosses HBM once per sweep).  1: a step is one
+ *                 launch of the fused step kernel, which sweeps both
+ *                 directions of a tile of 60 columns x 32 rows held in
+ *                 shared memory (its input box with 2 halo cells on each
+ *                 side crosses HBM once per step; the halo rows or columns
+ *                 are swept by both tiles that hold them).  Same results
+ *                 bit for bit; tile_len and span_len do not apply.
  * tile_len = 0 (default) and span_len = 0 take the tile length with the
  * best makespan of a list-scheduling model of the tile queue on the
  * resident warps (uniform cost per cell).  In FP64 contexts tile_len = 0
@@ -112,6 +120,7 @@ typedef struct {
     int ctas_per_sm;
     int graph_steps;
     int span_len;
+    int fused;
 } hydro_tuning;
 
 /* Counters kept on the device since hydro_init (hydro_stats()).
@@ -123,12 +132,16 @@ typedef struct {
  *                  hydro_set_state)
  *   kernel_launches  kernels the step calls launched (host count; a step of
  *                  an FP64 context launches 5 with adaptive y tiles, of an
- *                  FP32 context 5) */
+ *                  FP32 context 5; a fused step 3)
+ *   wait_site, wait_tile  the first bounded wait that gave up since the last
+ *                  hydro_set_state: kernel (0 none, 1 x sweep, 2 y sweep,
+ *                  3 fused step, 4 its FP32 second pass) and work-list tile */
 typedef struct {
     long long steps;
     long long riemann_fp64;
     unsigned int status_flags;
     long long kernel_launches;
+    int wait_site, wait_tile;
 } hydro_stats;
 
 /* Create a context (the "2D grid buffer for conservative variables" of
@@ -170,6 +183,18 @@ hydro_status hydro_set_state(hydro_ctx *ctx, int grid, const double *U, int on_d
 /* Copy the current state of grid `grid` into U_out (host or device,
  * [4][ny][nx] FP64).  Synchronises the context's stream. */
 hydro_status hydro_get_state(hydro_ctx *ctx, int grid, double *U_out, int on_device);
+
+/* Rows [row0, row0 + nrows) of grid `grid`: write them from U (host or
+ * device, FP64 [4][nrows][nx], x fastest), or read them into U_out.  Used
+ * to exchange the ghost rows of a grid split into slabs across processes
+ * (the subdomain interface buffers of §5, Fig. 10; the Coarse-Grain
+ * decomposition of §3): hydro_set_rows then recomputes the grid's CFL wave
+ * speed over all its cells (so hydro_cfl_dt and the next step's dt see the
+ * new rows), and changes neither the step counter nor the time.  FP32
+ * contexts round U to FP32.  HYDRO_EINVAL for rows outside the grid.
+ * Synchronise the context's stream. */
+hydro_status hydro_set_rows(hydro_ctx *ctx, int grid, int row0, int nrows, const double *U, int on_device);
+hydro_status hydro_get_rows(hydro_ctx *ctx, int grid, int row0, int nrows, double *U_out, int on_device);
 
 /* Advance every grid by nsteps steps (§1, Fig. 5).  Step k (counted from the
  * last hydro_set_state) sweeps x then y when k is even and y then x when k

@@ -25,7 +25,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC"
 FAST_F32 = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
 EXTRA = {"sweep_f32.cu": FAST_F32, "aux.cu": FAST_F32}
 SOURCES = ["hydro_abi.cu", "aux.cu", "sweep_f64.cu", "sweep_f32.cu", "noalloc.cu"]
-HEADERS = ["godunov.cuh", "kernels.h", "sweep_tma.cuh"]
+HEADERS = ["godunov.cuh", "kernels.h", "sweep_tma.cuh", "fused_tma.cuh"]
 
 
 def nvcc() -> str:

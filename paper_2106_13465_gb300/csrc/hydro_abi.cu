@@ -86,8 +86,8 @@ struct hydro_ctx {
     void* buf[2] = {nullptr, nullptr};
     size_t buf_elems = 0;
     GridDesc* d_grids = nullptr;
-    Tile* d_tiles[2] = {nullptr, nullptr};
-    int ntiles[2] = {0, 0};
+    Tile* d_tiles[3] = {nullptr, nullptr, nullptr};  // work lists: x, y, fused step
+    int ntiles[3] = {0, 0, 0};
     GridRun* d_run = nullptr;
     DevCounters* d_ctr = nullptr;
     double* d_stage = nullptr;  // FP64 [4][ny][nx] staging (FP32 contexts)
@@ -109,15 +109,18 @@ struct hydro_ctx {
     bool y_adaptive = false;        // y tiles cut from recorded costs every step
     double y_cap = 0.0;             // adaptive y tiles: cost cap / total recorded cost
     int redo_cap = 0;
-    int ctas_redo[2] = {0, 0};
-    hydro_tuning tuning{kDefaultTileLen, 0, kDefaultGraphSteps, 0};
-    int ctas[2] = {0, 0};       // CTAs per sweep launch (x, y)
+    int ctas_redo[3] = {0, 0, 0};
+    hydro_tuning tuning{kDefaultTileLen, 0, kDefaultGraphSteps, 0, 0};
+    int ctas[3] = {0, 0, 0};    // CTAs per launch (x sweep, y sweep, fused step)
     int tile_len_used[2] = {0, 0};
     long long step = 0;         // steps since the last hydro_set_state
     long long launches = 0;     // kernels launched by the step calls since hydro_init
     unsigned wait_limit = kWaitLimit;  // polls of a TMA completion before a sweep warp gives up
+    int cur = 0;                // state buffer holding the current state (a fused
+                                // step moves it to the other buffer)
     cudaGraphExec_t gexec = nullptr;
     int gexec_steps = 0;
+    int gexec_cur = 0;          // `cur` the graph was captured for
     std::string err;
 };
 
@@ -207,6 +210,17 @@ void build_tiles(const std::vector<GridDesc>& gd, int dir, int len, std::vector<
     }
 }
 
+// Fused step tiles: for each grid, x segment k (columns [60k - 2, 60k + 58))
+// times runs of kFusedRows rows.
+void build_fused_tiles(const std::vector<GridDesc>& gd, std::vector<Tile>& out) {
+    out.clear();
+    for (int g = 0; g < (int)gd.size(); ++g) {
+        const int ns = x_segments(gd[g].nx);
+        for (int y0 = 0; y0 < gd[g].ny; y0 += kFusedRows)
+            for (int k = 0; k < ns; ++k) out.push_back(Tile{g, k, y0, std::min(kFusedRows, gd[g].ny - y0)});
+    }
+}
+
 // Cost of a tile in cell units for the scheduling model: y, its cells plus
 // its 4-cell halo; x, the 64 cells of each of its segments plus a start-up.
 double tile_cost(const Tile& t, int dir) {
@@ -257,7 +271,7 @@ hydro_status build_tensor_maps(hydro_ctx* c) {
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
         return fail(c, HYDRO_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    const size_t nmaps = c->gd.size() * 4;
+    const size_t nmaps = c->gd.size() * 2 * kMapKinds;
     std::vector<CUtensorMap> maps(nmaps);
     const CUtensorMapDataType dtype = c->prec == 64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     for (size_t g = 0; g < c->gd.size(); ++g) {
@@ -267,9 +281,10 @@ hydro_status build_tensor_maps(hydro_ctx* c) {
         const cuuint32_t estr[3] = {1, 1, 1};
         for (int b = 0; b < 2; ++b) {
             void* base = (char*)c->buf[b] + (size_t)d.off * c->esz;
-            for (int dir = 0; dir < 2; ++dir) {
-                const cuuint32_t box[3] = {dir == DIR_X ? (cuuint32_t)kXSegment : 32u, dir == DIR_X ? 1u : 4u, 4u};
-                CUresult r = encode(&maps[(g * 2 + b) * 2 + dir], dtype, 3, base, dims, strides, box, estr,
+            for (int dir = 0; dir < kMapKinds; ++dir) {
+                const cuuint32_t box[3] = {dir == DIR_Y ? 32u : (cuuint32_t)kXSegment,
+                                           dir == DIR_X ? 1u : (dir == DIR_Y ? 4u : (cuuint32_t)kFusedBoxRows), 4u};
+                CUresult r = encode(&maps[map_index((int)g, b, dir)], dtype, 3, base, dims, strides, box, estr,
                                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
                 if (r != CUDA_SUCCESS) {
@@ -362,8 +377,30 @@ hydro_status upload_tiles(hydro_ctx* c) {
             c->ctas_redo[d] = std::max(1, std::min(need, c->nsm * occ2));
         }
     }
+    {
+        // fused step tiles (used when tuning.fused is set)
+        std::vector<Tile> t;
+        build_fused_tiles(c->gd, t);
+        if (c->d_tiles[DIR_FUSED]) cudaFree(c->d_tiles[DIR_FUSED]);
+        c->d_tiles[DIR_FUSED] = nullptr;
+        HCK(c, cudaMalloc(&c->d_tiles[DIR_FUSED], sizeof(Tile) * t.size()));
+        HCK(c, cudaMemcpy(c->d_tiles[DIR_FUSED], t.data(), sizeof(Tile) * t.size(), cudaMemcpyHostToDevice));
+        c->ntiles[DIR_FUSED] = (int)t.size();
+        const int var = c->prec == 64 ? VAR_F64 : VAR_F32_MAIN;
+        const int occ = c->prec == 64 ? fused_ctas_per_sm<double>(var) : fused_ctas_per_sm<float>(var);
+        if (occ <= 0) return fail(c, HYDRO_ECUDA, "fused step kernel cannot be resident on an SM");
+        int per_sm = c->tuning.ctas_per_sm;
+        if (per_sm <= 0 || per_sm > occ) per_sm = occ;
+        c->ctas[DIR_FUSED] = std::max(1, std::min(c->ntiles[DIR_FUSED], c->nsm * per_sm));
+        if (c->prec == 32) {
+            const int occ2 = fused_ctas_per_sm<float>(VAR_F32_REDO);
+            if (occ2 <= 0) return fail(c, HYDRO_ECUDA, "fused second-pass kernel cannot be resident on an SM");
+            c->ctas_redo[DIR_FUSED] = std::max(1, std::min(c->ntiles[DIR_FUSED], c->nsm * occ2));
+        }
+    }
+    const int max_tiles = std::max(c->ntiles[DIR_FUSED], std::max(c->ntiles[0], c->ntiles[1]));
     if (c->prec == 64) {
-        const int cap = std::max(c->ntiles[0], c->ntiles[1]);
+        const int cap = max_tiles;
         if (cap > c->tile_smax_cap) {
             cudaFree(c->d_tile_smax);
             c->d_tile_smax = nullptr;
@@ -373,7 +410,7 @@ hydro_status upload_tiles(hydro_ctx* c) {
         }
     }
     if (c->prec == 32) {
-        const int cap = std::max(c->ntiles[0], c->ntiles[1]);
+        const int cap = max_tiles;
         if (cap > c->redo_cap) {
             cudaFree(c->d_redo);
             c->d_redo = nullptr;
@@ -394,8 +431,8 @@ void drop_graph(hydro_ctx* c) {
 template <class T>
 SweepArgs<T> sweep_args(hydro_ctx* c, int which, const Consts<T>& K) {
     SweepArgs<T> a;
-    a.src = (const T*)c->buf[which];
-    a.dst = (T*)c->buf[which ^ 1];
+    a.src = (const T*)c->buf[c->cur ^ which];
+    a.dst = (T*)c->buf[c->cur ^ which ^ 1];
     a.grids = c->d_grids;
     a.tiles = nullptr;
     a.maps = c->d_maps;
@@ -408,7 +445,7 @@ SweepArgs<T> sweep_args(hydro_ctx* c, int which, const Consts<T>& K) {
     a.tile_smax = c->d_tile_smax;
     a.wait_limit = c->wait_limit;
     a.which = which;
-    a.src_buf = which;
+    a.src_buf = c->cur ^ which;
     a.redo_list = c->d_redo;
     a.redo_cap = c->redo_cap;
     a.run = c->d_run;
@@ -418,11 +455,44 @@ SweepArgs<T> sweep_args(hydro_ctx* c, int which, const Consts<T>& K) {
     return a;
 }
 
+// Enqueue one fused step (fused_tma.cuh): the dt prologue, the step kernel
+// from buf[cur] to buf[cur ^ 1], and (FP64) the exact CFL pass over the new
+// state or (FP32) the near-vacuum second pass; the state then lives in
+// buf[cur ^ 1].  ev as in enqueue_step_t (the second interval is empty).
+template <class T>
+cudaError_t enqueue_fused_step_t(hydro_ctx* c, int parity, const double* ovr, double* log, cudaStream_t s,
+                                 const Consts<T>& K, cudaEvent_t* ev) {
+    cudaError_t e;
+    if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
+    e = launch_step_prologue(c->d_run, c->d_grids, (int)c->gd.size(), c->d_ctr, ovr, c->cfl, log, s);
+    if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
+    SweepArgs<T> a = sweep_args<T>(c, 0, K);
+    a.which = 1;  // the new state's CFL speed is folded in
+    a.tiles = c->d_tiles[DIR_FUSED];
+    a.ntiles = c->ntiles[DIR_FUSED];
+    if (sizeof(T) == 8) {
+        e = launch_fused<T>(parity, VAR_F64, a, c->ctas[DIR_FUSED], s);
+        if (e == cudaSuccess)
+            e = launch_cfl_fp64((const double*)a.dst, c->d_grids, a.tiles, a.ntiles, nullptr, DIR_FUSED,
+                                c->d_tile_smax, c->d_run, c->d_ctr, c->Kd, c->nsm * 8, s);
+    } else {
+        e = launch_fused<T>(parity, VAR_F32_MAIN, a, c->ctas[DIR_FUSED], s);
+        if (e == cudaSuccess) e = launch_fused<T>(parity, VAR_F32_REDO, a, c->ctas_redo[DIR_FUSED], s);
+    }
+    if (e != cudaSuccess) return e;
+    c->cur ^= 1;
+    if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
 // Enqueue one step of parity `parity` on stream s; ev (optional, 4 events)
 // brackets the three launches for timing.
 template <class T>
 cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* log,
                            cudaStream_t s, const Consts<T>& K, cudaEvent_t* ev) {
+    if (c->tuning.fused) return enqueue_fused_step_t<T>(c, parity, ovr, log, s, K, ev);
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
     e = launch_step_prologue(c->d_run, c->d_grids, (int)c->gd.size(), c->d_ctr, ovr, c->cfl, log, s);
@@ -447,7 +517,7 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
             e = launch_sweep<T>(dir, VAR_F64, a, c->ctas[dir], s);
             // the second sweep's new state: its max wave speed (next dt)
             if (e == cudaSuccess && which == 1)
-                e = launch_cfl_fp64((const double*)c->buf[0], c->d_grids, a.tiles, a.ntiles, a.ntiles_dev, dir,
+                e = launch_cfl_fp64((const double*)c->buf[c->cur], c->d_grids, a.tiles, a.ntiles, a.ntiles_dev, dir,
                                     c->d_tile_smax, c->d_run, c->d_ctr, c->Kd, c->nsm * 8, s);
         } else {
             // main FP32 pass, then the second pass over tiles it queued
@@ -462,8 +532,10 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
 
 // Kernels one step launches (enqueue_step_t): the dt prologue, the y tiler
 // (adaptive y tiles), and per sweep the sweep kernel plus, FP64, the CFL
-// pass after the second sweep or, FP32, the near-vacuum second pass.
+// pass after the second sweep or, FP32, the near-vacuum second pass.  A
+// fused step: the prologue, the step kernel and the CFL or second pass.
 int launches_per_step(const hydro_ctx* c) {
+    if (c->tuning.fused) return 3;
     return 1 + (c->y_adaptive ? 1 : 0) + (c->prec == 64 ? 2 + 1 : 2 * 2);
 }
 
@@ -474,13 +546,17 @@ cudaError_t enqueue_step(hydro_ctx* c, int parity, const double* ovr, double* lo
 }
 
 hydro_status ensure_graph(hydro_ctx* c, int steps) {
-    if (c->gexec && c->gexec_steps == steps) return HYDRO_OK;
+    if (c->gexec && c->gexec_steps == steps && c->gexec_cur == c->cur) return HYDRO_OK;
     drop_graph(c);
     cudaGraph_t graph = nullptr;
     HCK(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
+    // the captured steps move `cur` as they will when the graph runs; an even
+    // number of steps brings it back
+    const int cur0 = c->cur;
     for (int k = 0; k < steps && e == cudaSuccess; ++k)
         e = enqueue_step(c, k & 1, nullptr, nullptr, c->capture_stream);
+    c->cur = cur0;
     cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &graph);
     if (e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -494,6 +570,7 @@ hydro_status ensure_graph(hydro_ctx* c, int steps) {
         return fail_cuda(c, "cudaGraphInstantiate", e);
     }
     c->gexec_steps = steps;
+    c->gexec_cur = cur0;
     return HYDRO_OK;
 }
 
@@ -504,7 +581,7 @@ hydro_status check_grid(hydro_ctx* c, int grid) {
 }
 
 template <class T>
-T* state_ptr(hydro_ctx* c) { return (T*)c->buf[0]; }
+T* state_ptr(hydro_ctx* c) { return (T*)c->buf[c->cur]; }
 
 hydro_status status_result(hydro_ctx* c, unsigned int status) {
     if (status & STATUS_BAD_TILE)
@@ -627,7 +704,7 @@ void hydro_destroy(hydro_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graph(c);
     for (int b = 0; b < 2; ++b) cudaFree(c->buf[b]);
-    for (int d = 0; d < 2; ++d) cudaFree(c->d_tiles[d]);
+    for (int d = 0; d < 3; ++d) cudaFree(c->d_tiles[d]);
     cudaFree(c->d_grids);
     cudaFree(c->d_run);
     cudaFree(c->d_ctr);
@@ -657,6 +734,7 @@ hydro_status hydro_set_tuning(hydro_ctx* c, const hydro_tuning* t) {
     if (n.ctas_per_sm < 0 || n.ctas_per_sm > 64) return fail(c, HYDRO_EINVAL, "ctas_per_sm must be in [0, 64]");
     if (n.graph_steps < 0 || (n.graph_steps & 1) || n.graph_steps > 1000)
         return fail(c, HYDRO_EINVAL, "graph_steps must be even and in [0, 1000]");
+    if (n.fused != 0 && n.fused != 1) return fail(c, HYDRO_EINVAL, "fused must be 0 or 1");
     HCK(c, cudaStreamSynchronize(c->stream));
     c->tuning = n;
     drop_graph(c);
@@ -693,6 +771,7 @@ hydro_status hydro_set_state(hydro_ctx* c, int grid, const double* U, int on_dev
     // time of this grid, step counter and status flags restart
     HCK(c, cudaMemsetAsync(&c->d_run[grid].t, 0, sizeof(double), c->stream));
     HCK(c, cudaMemsetAsync(&c->d_ctr->status, 0, sizeof(unsigned int), c->stream));
+    HCK(c, cudaMemsetAsync(&c->d_ctr->wait_site, 0, 2 * sizeof(int), c->stream));
     HCK(c, cudaStreamSynchronize(c->stream));
     c->step = 0;
     return HYDRO_OK;
@@ -711,6 +790,59 @@ hydro_status hydro_get_state(hydro_ctx* c, int grid, double* U, int on_device) {
     } else {
         HCK(c, launch_unpack<float>(state_ptr<float>(c), c->d_stage, g, c->stream));
         HCK(c, cudaMemcpyAsync(U, c->d_stage, sizeof(double) * 4 * g.nx * (size_t)g.ny, kind, c->stream));
+    }
+    HCK(c, cudaStreamSynchronize(c->stream));
+    return HYDRO_OK;
+}
+
+hydro_status hydro_set_rows(hydro_ctx* c, int grid, int row0, int nrows, const double* U, int on_device) {
+    hydro_status st = check_grid(c, grid);
+    if (st != HYDRO_OK) return st;
+    if (!U) return fail(c, HYDRO_EINVAL, "U is NULL");
+    const GridDesc& g = c->gd[grid];
+    if (row0 < 0 || nrows < 1 || row0 + nrows > g.ny) return fail(c, HYDRO_EINVAL, "rows out of range");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t n = (size_t)g.nx * nrows;
+    if (c->prec == 64) {
+        for (int q = 0; q < 4; ++q)
+            HCK(c, cudaMemcpy2DAsync(state_ptr<double>(c) + g.off + q * g.plane + (long long)row0 * g.pitch,
+                                     sizeof(double) * g.pitch, U + q * n, sizeof(double) * g.nx,
+                                     sizeof(double) * g.nx, (size_t)nrows, kind, c->stream));
+        HCK(c, launch_cfl_init<double>(state_ptr<double>(c), c->d_grids, grid, g, c->d_run, c->d_ctr, c->Kd,
+                                       c->stream));
+    } else {
+        GridDesc rows = g;  // the row band as a grid of nrows rows
+        rows.off = g.off + (long long)row0 * g.pitch;
+        rows.ny = nrows;
+        HCK(c, cudaMemcpyAsync(c->d_stage, U, sizeof(double) * 4 * n, kind, c->stream));
+        HCK(c, launch_pack<float>(c->d_stage, state_ptr<float>(c), rows, c->stream));
+        HCK(c, launch_cfl_init<float>(state_ptr<float>(c), c->d_grids, grid, g, c->d_run, c->d_ctr, c->Kf,
+                                      c->stream));
+    }
+    HCK(c, cudaStreamSynchronize(c->stream));
+    return HYDRO_OK;
+}
+
+hydro_status hydro_get_rows(hydro_ctx* c, int grid, int row0, int nrows, double* U, int on_device) {
+    hydro_status st = check_grid(c, grid);
+    if (st != HYDRO_OK) return st;
+    if (!U) return fail(c, HYDRO_EINVAL, "U_out is NULL");
+    const GridDesc& g = c->gd[grid];
+    if (row0 < 0 || nrows < 1 || row0 + nrows > g.ny) return fail(c, HYDRO_EINVAL, "rows out of range");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t n = (size_t)g.nx * nrows;
+    if (c->prec == 64) {
+        for (int q = 0; q < 4; ++q)
+            HCK(c, cudaMemcpy2DAsync(U + q * n, sizeof(double) * g.nx,
+                                     state_ptr<double>(c) + g.off + q * g.plane + (long long)row0 * g.pitch,
+                                     sizeof(double) * g.pitch, sizeof(double) * g.nx, (size_t)nrows, kind,
+                                     c->stream));
+    } else {
+        GridDesc rows = g;
+        rows.off = g.off + (long long)row0 * g.pitch;
+        rows.ny = nrows;
+        HCK(c, launch_unpack<float>(state_ptr<float>(c), c->d_stage, rows, c->stream));
+        HCK(c, cudaMemcpyAsync(U, c->d_stage, sizeof(double) * 4 * n, kind, c->stream));
     }
     HCK(c, cudaStreamSynchronize(c->stream));
     return HYDRO_OK;
@@ -883,6 +1015,8 @@ hydro_status hydro_get_stats(hydro_ctx* c, hydro_stats* out) {
     out->riemann_fp64 = (long long)ctr.riemann_fp64;
     out->status_flags = ctr.status;
     out->kernel_launches = c->launches;
+    out->wait_site = ctr.wait_site;
+    out->wait_tile = ctr.wait_tile;
     return HYDRO_OK;
 }
 

@@ -11,13 +11,24 @@
 // Interior cells only: the 2 ghost cells per side along the sweep axis are
 // formed while a line is read (boundary conditions folded into the load).
 //
-// Each grid and buffer also has two TMA tensor maps over this layout, a 3D
+// Each grid and buffer also has three TMA tensor maps over this layout, a 3D
 // tensor (x, y, q) of extents (nx, ny, 4) with byte strides
 // (pitch * esz, plane * esz):
 //   x-sweep map: box (64 cells, 1 row, 4 planes)    -- one row segment,
 //                starting at x = -4 + 60 k
 //   y-sweep map: box (32 columns, 4 rows, 4 planes) -- 32 columns x 4 cells
-// stored at maps[(grid * 2 + buffer) * 2 + dir].
+//   fused map:   box (64 cells, kFusedRows + 4 rows, 4 planes) -- the input
+//                of a fused step tile (below)
+// stored at maps[map_index(grid, buffer, kind)].
+//
+// Fused step (one kernel per step instead of two sweeps).  A tile is the
+// 60 columns [60 k - 2, 60 k + 58) of one x segment times up to kFusedRows
+// rows [y0, y0 + rows); its input box is the 64 columns of the segment times
+// rows [y0 - 2, y0 + rows + 2), loaded by one TMA copy into shared memory.
+// The first sweep of the step runs on the box in place (x first: every box
+// row, i.e. the tile's rows and 2 halo rows on each side; y first: every box
+// column), the second writes the tile's cells to the other state buffer.
+// Stored as (grid, line0 = k, cell0 = y0, ncell = rows).
 //
 // Work lists.  y sweep: a tile is 32 columns (one per lane) x ncell rows.
 // x sweep: a tile is a run of consecutive segments of one row, stored as
@@ -51,7 +62,7 @@
 namespace hydro {
 
 enum { BC_REFLECT = 0, BC_TRANSMISSIVE = 1, BC_PERIODIC = 2 };
-enum { DIR_X = 0, DIR_Y = 1 };
+enum { DIR_X = 0, DIR_Y = 1, DIR_FUSED = 2 };  // also the kinds of tensor map and work list
 enum { STATUS_BAD_RHO = 1u, STATUS_BAD_E = 2u, STATUS_TIMEOUT = 4u, STATUS_BAD_TILE = 8u };
 
 // kernel variants: FP64; FP32 main pass (tiles with a near-vacuum interface
@@ -68,11 +79,27 @@ constexpr int kSweepThreads = 128;  // threads per CTA of the sweep kernels
 // (the default of SweepArgs::wait_limit, and the bound of the wait for the
 // copies still in flight after a timeout)
 constexpr unsigned kWaitLimit = 1u << 22;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // ... and at most about a second
 
 // TMA ring geometry per warp.  x sweep: one slot holds a 64-cell segment of
 // one row, 4 planes; y sweep: one slot holds 4 rows x 32 columns, 4 planes.
 constexpr int kXSegment = 64;  // cells per x segment (2 per lane)
 constexpr int kXStride = 60;   // segments overlap by 4 cells; 60 results each
+constexpr int kFusedRows = 32;                  // output rows of a fused tile
+constexpr int kFusedBoxRows = kFusedRows + 4;   // rows of its input box
+constexpr int kFusedThreads = 128;              // threads per CTA of the fused kernel
+constexpr int kMapKinds = 3;                    // tensor maps per grid and buffer
+__host__ __device__ constexpr size_t map_index(int grid, int buffer, int kind) {
+    return ((size_t)grid * 2 + buffer) * kMapKinds + kind;
+}
+template <class T>
+__host__ __device__ constexpr int fused_box_bytes() {
+    return 4 * kFusedBoxRows * kXSegment * (int)sizeof(T);
+}
+template <class T>
+__host__ __device__ constexpr int fused_smem_bytes() {
+    return fused_box_bytes<T>() + 16;  // the box and its mbarrier
+}
 __host__ __device__ constexpr int ring_slots(int dir) { return 4; }
 template <class T>
 __host__ __device__ constexpr int slot_bytes(int dir) {
@@ -128,6 +155,8 @@ struct DevCounters {
     unsigned long long ycost_total[2];    // recorded y-sweep work, by step parity
     unsigned int ycost_max[2];            // largest recorded work of a y tile, by step parity
     unsigned int sm_slot[kMaxSmIds];      // y sweep: warps that have started on each SM
+    int wait_site;                        // the first wait that gave up: kernel (1 x, 2 y,
+    int wait_tile;                        // 3 fused, 4 fused second pass) and its tile
 };
 
 template <class T>
@@ -172,7 +201,7 @@ int sweep_ctas_per_sm(int dir, int var);
 // estimate is within 2e-3 of the exact speed (relative), well inside
 // kCflScreen / 2, so the cell of the exact maximum is always evaluated.
 // tiles / ntiles / ntiles_dev / dir describe the second sweep's work list as
-// in SweepArgs.
+// in SweepArgs (dir DIR_FUSED: the fused step's tile list).
 constexpr float kCflScreen = 1e-2f;
 cudaError_t launch_cfl_fp64(const double* state, const GridDesc* grids, const Tile* tiles, int ntiles,
                             const unsigned int* ntiles_dev, int dir, const unsigned int* tile_smax,
@@ -188,6 +217,17 @@ cudaError_t launch_cfl_screened_fp64(const double* state, const GridDesc& gd, in
 
 template <class T>
 cudaError_t launch_sweep(int dir, int var, const SweepArgs<T>& a, int nctas, cudaStream_t s);
+
+// Fused step: both sweeps of a step in one launch over the fused tile list
+// (a.tiles, a.ntiles); order 0 sweeps x then y, order 1 y then x.  a.src is
+// the state at the start of the step, a.dst receives the new state; the
+// CFL wave speed of the new state is folded in as by the second sweep.
+template <class T>
+cudaError_t launch_fused(int order, int var, const SweepArgs<T>& a, int nctas, cudaStream_t s);
+
+// Resident CTAs per SM of the fused kernel (and raise its shared-memory limit).
+template <class T>
+int fused_ctas_per_sm(int var);
 
 // Cut the adaptive y tiles from the recorded work: each of the nstat tiles
 // of the static tiling `stat` (whole cost blocks) is split where its pieces'

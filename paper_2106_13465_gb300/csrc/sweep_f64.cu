@@ -1,9 +1,9 @@
-// sweep_f64.cu -- FP64 instantiation of the fused sweep kernel, and the FP64
-// CFL passes.  FP64 additions, multiplications, fused multiply-adds and
+// sweep_f64.cu -- FP64 instantiations of the sweep kernels and of the fused
+// step kernel, and the FP64 CFL passes.  FP64 additions, multiplications, fused multiply-adds and
 // square roots are IEEE; divisions go through a refined FP32 reciprocal and
 // the rarefaction power through a 7th root (gamma = 7/5) or exp2/log2, each
 // within a few ulp (godunov.cuh: trcp, root7, pow_z).
-#include "sweep_tma.cuh"
+#include "fused_tma.cuh"
 
 namespace hydro {
 
@@ -59,6 +59,12 @@ __global__ void __launch_bounds__(256) cfl_refine_kernel(const double* __restric
             const int x0 = max(0, kXStride * tile.cell0 - 2);
             const int x1 = min(g.nx, kXStride * (tile.cell0 + tile.ncell) - 2);
             for (int x = x0 + lane; x < x1; x += 32) visit(x, tile.line0);
+        } else if (dir == DIR_FUSED) {
+            // columns [60 line0 - 2, 60 line0 + 58) of rows cell0 .. cell0 + ncell - 1
+            const int x0 = max(0, kXStride * tile.line0 - 2);
+            const int x1 = min(g.nx, kXStride * tile.line0 + kXStride - 2);
+            for (int j = tile.cell0; j < tile.cell0 + tile.ncell; ++j)
+                for (int x = x0 + lane; x < x1; x += 32) visit(x, j);
         } else {
             const int col = tile.line0 + lane;
             if (col < g.nx)
@@ -120,6 +126,19 @@ cudaError_t launch_cfl_screened_fp64(const double* state, const GridDesc& gd, in
     cfl_grid_kernel<0><<<(int)nb, 256, 0, s>>>(state, gd, grid, run, ctr, K);
     cfl_grid_kernel<1><<<(int)nb, 256, 0, s>>>(state, gd, grid, run, ctr, K);
     return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_fused<double>(int order, int var, const SweepArgs<double>& a, int nctas, cudaStream_t s) {
+    (void)var;
+    if (nctas <= 0) return cudaSuccess;
+    return launch_fused_var<double, VAR_F64>(order, a, nctas, s);
+}
+
+template <>
+int fused_ctas_per_sm<double>(int var) {
+    (void)var;
+    return fused_occupancy<double, VAR_F64>();
 }
 
 template <>

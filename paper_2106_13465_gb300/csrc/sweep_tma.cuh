@@ -66,9 +66,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// At most `limit` polls and about kWaitNs nanoseconds (a poll may suspend
+// the thread for a while), whichever comes first.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit = kWaitLimit) {
-    for (unsigned it = 0; it < limit; ++it)
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u && global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
@@ -277,6 +287,11 @@ __device__ __forceinline__ float cfl_estimate(const Consts<double>& K, double r,
     p = (p < pm) ? pm : p;
     const float c = sqrtf(gam * p * ir);
     return fmaxf(fabsf(u), fabsf(v)) + c;
+}
+
+// Record the first wait that gave up (kernel site, tile); one thread calls it.
+__device__ __forceinline__ void record_wait_site(DevCounters* ctr, int site, int tile) {
+    if (atomicCAS(&ctr->wait_site, 0, site) == 0) ctr->wait_tile = tile;
 }
 
 // Claim the next tile: the main pass takes the work list in order, the FP32
@@ -495,7 +510,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
         const int s0 = tile.cell0, s1 = tile.cell0 + tile.ncell;
         const int kfirst = s0 - 2, klast = s1 + 1;
         const int nch = (klast - kfirst) / C + 1;
-        const CUtensorMap* msrc = a.maps + ((size_t)tile.grid * 2 + a.src_buf) * 2 + DIR_Y;
+        const CUtensorMap* msrc = a.maps + map_index(tile.grid, a.src_buf, DIR_Y);
         if (lane == 0)
             for (int c = 0; c < S && c < nch; ++c) ring.issue(c, msrc, line0, kfirst + c * C);
 
@@ -519,7 +534,11 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
 
         for (int c = 0; c < nch; ++c) {
             const int sl = c % S;
-            if (!ring.wait(sl, lane, a.wait_limit)) { aborted = true; break; }
+            if (!ring.wait(sl, lane, a.wait_limit)) {
+                aborted = true;
+                if (lane == 0) record_wait_site(a.ctr, 2, t);
+                break;
+            }
             const T* sp = reinterpret_cast<const T*>(ring.slot(sl));
             const int kc = kfirst + c * C;
             int j0 = 0;
@@ -736,6 +755,82 @@ __device__ __forceinline__ void store_pair(T* __restrict__ p, long long plane, c
     }
 }
 
+// Lane mapping of a 64-cell x segment: lane l holds the cells at segment
+// positions pos(l, 0) = 2l and pos(l, 1) = 2l+1.  The results are the
+// positions 2 .. 61 (the others only feed them); every interface is solved
+// once.  (A mapping of lane l to positions l and l+32, which gives each
+// Riemann solve of a warp 32 consecutive interfaces instead of every other
+// one of 64, was measured 6-7 % slower in FP64 and is not used.)
+template <class T>
+struct XMap {
+    static __device__ __forceinline__ int pos(int lane, int j) { return 2 * lane + j; }
+    static __device__ __forceinline__ int lane_of(int p) { return p >> 1; }
+    static __device__ __forceinline__ int cell_of(int p) { return p & 1; }
+};
+
+// The arithmetic of one segment: lane l holds the conserved states u0, u1 of
+// its cells A = 2l and B = 2l+1 (ghosts already in place) and returns their
+// updated states n0, n1 (meaningful at positions 2 .. 61) and the
+// second-pass requests of its two Riemann problems A-1/2 (r0) and A+1/2
+// (r1).  It takes the primitives of A-1 and the right face of A-1 from lane
+// l-1, the primitives of B+1 and the flux at B+1/2 from lane l+1.  Lanes 0
+// and 31 have no left / right neighbour in the segment and hold no result;
+// they mirror their own cells so their throw-away Riemann problems stay
+// mild and do not stretch the warp's Newton loop.
+template <class T, int VAR>
+__device__ __forceinline__ void segment_update(const SweepArgs<T>& a, T dtdx, T hdtdx, int lane,
+                                               const Cons<T>& u0, const Cons<T>& u1, Cons<T>& n0,
+                                               Cons<T>& n1, bool& r0, bool& r1, unsigned& nfb) {
+    const Consts<T>& K = a.K;
+    unsigned wk = 0;  // scheduling work estimate, unused in x
+    T ir0, ir1;
+    const Prim<T> W0 = cons_to_prim(K, u0, ir0);
+    const Prim<T> W1 = cons_to_prim(K, u1, ir1);
+    Prim<T> Wm = shfl_up1(W1);    // cell A-1
+    Prim<T> Wp = shfl_down1(W0);  // cell B+1
+    if (lane == 0) Wm = W0;
+    if (lane == 31) Wp = W1;
+    Prim<T> WLA, WRA, WLB, WRB;
+    trace(K, hdtdx, Wm, W0, ir0, W1, WLA, WRA);  // cell A
+    trace(K, hdtdx, W0, W1, ir1, Wp, WLB, WRB);  // cell B
+    Prim<T> WRm = shfl_up1(WRB);  // right face of A-1
+    if (lane == 0) WRm = WLA;
+    const Cons<T> Fm = FluxOp<T, VAR>::eval(a, WRm, WLA, r0, nfb, wk);  // A - 1/2
+    const Cons<T> Fc = FluxOp<T, VAR>::eval(a, WRA, WLB, r1, nfb, wk);  // A + 1/2
+    const Cons<T> Fp = shfl_down1(Fm);                                 // B + 1/2
+    n0 = update(u0, dtdx, Fc, Fm);
+    n1 = update(u1, dtdx, Fp, Fc);
+}
+
+// A cell at segment position p of the segment starting at x is a result
+// stored in a row of n cells.
+__device__ __forceinline__ bool seg_result(int p, int x, int n) {
+    return p >= 2 && p <= kXSegment - 3 && x + p >= 0 && x + p < n;
+}
+
+// Whether a lane's second-pass requests r0, r1 (segment_update) concern an
+// interface next to a stored result (every lane calls it: it shuffles).
+template <class T>
+__device__ __forceinline__ bool segment_redo(int lane, int x, int n, bool r0, bool r1) {
+    // A-1/2 and A+1/2 feed A and B; B+1/2 (lane l+1's r0) feeds B
+    const bool lo = seg_result(2 * lane, x, n), hi = seg_result(2 * lane + 1, x, n);
+    const bool r0n = __shfl_down_sync(0xffffffffu, r0, 1);
+    return ((r0 || r1) && lo) || (r0n && lo && hi);
+}
+
+// The lane's two cells from a segment laid out [plane][64] (ring slot).
+template <class T>
+__device__ __forceinline__ void read_seg(const unsigned char* slot, int lane, Cons<T>& u0, Cons<T>& u1) {
+    read_pair<T>(slot, 2 * lane, u0, u1);
+}
+
+// Store the lane's stored results (row pointer drow, segment start x).
+template <class T>
+__device__ __forceinline__ void store_seg(T* __restrict__ drow, long long plane, int lane, int x, bool v0, bool v1,
+                                          const Cons<T>& n0, const Cons<T>& n1) {
+    if (v0) store_pair<T>(drow + x + 2 * lane, plane, n0, n1, v0, v1);
+}
+
 template <class T, int VAR, int WHICH>
 __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::value))
     sweep_x_kernel(const SweepArgs<T> a) {
@@ -752,7 +847,6 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
     const unsigned acc = a.ctr->acc;
     unsigned kbad = 0, nfb = 0;
     bool aborted = false;
-    const bool inner = (lane >= 1) && (lane <= 30);  // lanes holding results
 
     for (;;) {
         const int t = claim_tile<T, VAR>(a, lane);
@@ -763,7 +857,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
         const int n = g.nx, row = tile.line0;
         const int k0 = tile.cell0, nseg = tile.ncell;
         const int bclo = g.bc[0], bchi = g.bc[1];
-        const CUtensorMap* msrc = a.maps + ((size_t)tile.grid * 2 + a.src_buf) * 2 + DIR_X;
+        const CUtensorMap* msrc = a.maps + map_index(tile.grid, a.src_buf, DIR_X);
         if (lane == 0)
             for (int c = 0; c < S && c < nseg; ++c) ring.issue(c, msrc, -4 + STEP * (k0 + c), row);
 
@@ -778,10 +872,14 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
         for (int c = 0; c < nseg; ++c) {
             const int x = -4 + STEP * (k0 + c);
             const int sl = c % S;
-            if (!ring.wait(sl, lane, a.wait_limit)) { aborted = true; break; }
-            const int A = x + 2 * lane;
-            Cons<T> uA, uB;
-            read_pair<T>(ring.slot(sl), 2 * lane, uA, uB);
+            if (!ring.wait(sl, lane, a.wait_limit)) {
+                aborted = true;
+                if (lane == 0) record_wait_site(a.ctr, 1, t);
+                break;
+            }
+            const int P0 = XMap<T>::pos(lane, 0), P1 = XMap<T>::pos(lane, 1);
+            Cons<T> uA, uB;  // the cells at positions P0, P1
+            read_seg<T>(ring.slot(sl), lane, uA, uB);
             __syncwarp();
             if (lane == 0 && c + S < nseg) {
                 fence_proxy_async_smem();
@@ -792,34 +890,34 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
                 // transmissive: the mirror cells 1, 0 or n-1, n-2 lie in this
                 // segment, so they come by shuffle; periodic: the wrap-around
                 // cells come from global memory.
-                const int kA = A, kB = A + 1;
+                const int kA = x + P0, kB = x + P1;
                 const bool gA = (kA >= -2 && kA < 0) || (kA >= n && kA <= n + 1);
                 const bool gB = (kB >= -2 && kB < 0) || (kB >= n && kB <= n + 1);
                 const int bcA = (kA < 0) ? bclo : bchi, bcB = (kB < 0) ? bclo : bchi;
                 const bool mA = gA && bcA != BC_PERIODIC, mB = gB && bcB != BC_PERIODIC;
-                const int sA = mA ? ((kA < 0) ? -1 - kA : 2 * n - 1 - kA) - x : 2 * lane;
-                const int sB = mB ? ((kB < 0) ? -1 - kB : 2 * n - 1 - kB) - x : 2 * lane + 1;
-                const Cons<T> a0 = shfl_idx(uA, sA >> 1), a1 = shfl_idx(uB, sA >> 1);
-                const Cons<T> b0 = shfl_idx(uA, sB >> 1), b1 = shfl_idx(uB, sB >> 1);
-                if (mA) uA = flip((sA & 1) ? a1 : a0, bcA == BC_REFLECT);
+                const int sA = mA ? ((kA < 0) ? -1 - kA : 2 * n - 1 - kA) - x : P0;
+                const int sB = mB ? ((kB < 0) ? -1 - kB : 2 * n - 1 - kB) - x : P1;
+                const int lA = XMap<T>::lane_of(sA), lB = XMap<T>::lane_of(sB);
+                const Cons<T> a0 = shfl_idx(uA, lA), a1 = shfl_idx(uB, lA);
+                const Cons<T> b0 = shfl_idx(uA, lB), b1 = shfl_idx(uB, lB);
+                if (mA) uA = flip(XMap<T>::cell_of(sA) ? a1 : a0, bcA == BC_REFLECT);
                 else if (gA) uA = ghost_cell<T, DIR_X>(a.src, g, row, kA, n, bclo, bchi);
-                if (mB) uB = flip((sB & 1) ? b1 : b0, bcB == BC_REFLECT);
+                if (mB) uB = flip(XMap<T>::cell_of(sB) ? b1 : b0, bcB == BC_REFLECT);
                 else if (gB) uB = ghost_cell<T, DIR_X>(a.src, g, row, kB, n, bclo, bchi);
                 // positions beyond the boundary cells (zero-filled) take a copy
                 // of the nearest boundary cell: they feed no result, and equal
                 // states keep their throw-away Riemann problems trivial
                 const int lo2 = -2 - x, hi2 = n + 1 - x;  // segment positions of -2, n+1
                 const int pl = (lo2 > 0) ? lo2 : 0, ph = (hi2 < SEG - 1) ? hi2 : SEG - 1;
-                const Cons<T> cl0 = shfl_idx(uA, pl >> 1), cl1 = shfl_idx(uB, pl >> 1);
-                const Cons<T> ch0 = shfl_idx(uA, ph >> 1), ch1 = shfl_idx(uB, ph >> 1);
-                const Cons<T> cl = (pl & 1) ? cl1 : cl0, ch = (ph & 1) ? ch1 : ch0;
+                const Cons<T> cl0 = shfl_idx(uA, XMap<T>::lane_of(pl)), cl1 = shfl_idx(uB, XMap<T>::lane_of(pl));
+                const Cons<T> ch0 = shfl_idx(uA, XMap<T>::lane_of(ph)), ch1 = shfl_idx(uB, XMap<T>::lane_of(ph));
+                const Cons<T> cl = XMap<T>::cell_of(pl) ? cl1 : cl0, ch = XMap<T>::cell_of(ph) ? ch1 : ch0;
                 if (kA < -2) uA = cl;
                 if (kB < -2) uB = cl;
                 if (kA > n + 1) uA = ch;
                 if (kB > n + 1) uB = ch;
             }
-            const bool lo = inner && A >= 0 && A < n;
-            const bool hi = inner && A + 1 < n;
+            const bool v0 = seg_result(P0, x, n), v1 = seg_result(P1, x, n);
             if (Shortcuts<T>::stencil) {
                 // all 64 cells of the segment equal bit for bit (ghosts and
                 // fill included): every stencil is uniform, the traces return
@@ -827,47 +925,20 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
                 const Cons<T> ref = shfl_idx(uA, 0);
                 if (__all_sync(0xffffffffu, (diff_bits(uA, ref) | diff_bits(uB, ref)) == 0)) {
                     // one status and wave-speed check stands for all the copies
-                    const int first = __ffs(__ballot_sync(0xffffffffu, lo)) - 1;
-                    if (lo) {
-                        store_pair<T>(drow + A, g.plane, uA, uB, lo, hi);
-                        if (lane == first) check_cell<T, WHICH>(K, uA, tbad, smax, sbits);
-                    }
+                    const int first = __ffs(__ballot_sync(0xffffffffu, v0 || v1)) - 1;
+                    store_seg<T>(drow, g.plane, lane, x, v0, v1, uA, uB);
+                    if (lane == first) check_cell<T, WHICH>(K, uA, tbad, smax, sbits);
                     continue;
                 }
             }
-            T irA, irB;
-            const Prim<T> WA = cons_to_prim(K, uA, irA);
-            const Prim<T> WB = cons_to_prim(K, uB, irB);
-            // lanes 0 and 31 have no left / right neighbour in the segment and
-            // hold no result; they mirror their own cells so their throw-away
-            // Riemann problems stay mild and do not stretch the warp's Newton loop
-            Prim<T> Wm = shfl_up1(WB);    // cell A-1
-            Prim<T> Wp = shfl_down1(WA);  // cell B+1
-            if (lane == 0) Wm = WA;
-            if (lane == 31) Wp = WB;
-            Prim<T> WLA, WRA, WLB, WRB;
-            trace(K, hdtdx, Wm, WA, irA, WB, WLA, WRA);  // cell A
-            trace(K, hdtdx, WA, WB, irB, Wp, WLB, WRB);  // cell B
-            Prim<T> WRm = shfl_up1(WRB);  // right face of A-1
-            if (lane == 0) WRm = WLA;
-            bool r1 = false, r2 = false;
-            unsigned wk = 0;  // scheduling work estimate, unused in x
-            const Cons<T> Fm = FluxOp<T, VAR>::eval(a, WRm, WLA, r1, nfb, wk);  // A - 1/2
-            const Cons<T> Fc = FluxOp<T, VAR>::eval(a, WRA, WLB, r2, nfb, wk);  // A + 1/2
-            const Cons<T> Fp = shfl_down1(Fm);                              // B + 1/2
-            const Cons<T> nA = update(uA, dtdx, Fc, Fm);
-            const Cons<T> nB = update(uB, dtdx, Fp, Fc);
+            bool r0 = false, r1 = false;
+            Cons<T> nA, nB;
+            segment_update<T, VAR>(a, dtdx, hdtdx, lane, uA, uB, nA, nB, r0, r1, nfb);
             // a second-pass request counts only for interfaces feeding stored cells
-            redo |= (r1 || r2) && lo;
-            if (lo) {
-                store_pair<T>(drow + A, g.plane, nA, nB, lo, hi);
-                check_cell<T, WHICH>(K, nA, tbad, smax, sbits);
-                if (hi) check_cell<T, WHICH>(K, nB, tbad, smax, sbits);
-            }
-            // the flux at B+1/2 (from lane l+1) feeds B: ask for a second pass
-            // there too when lane l+1 solved it in FP32 near vacuum
-            const bool r1n = __shfl_down_sync(0xffffffffu, r1, 1);
-            redo |= r1n && lo && hi;
+            redo |= segment_redo<T>(lane, x, n, r0, r1);
+            store_seg<T>(drow, g.plane, lane, x, v0, v1, nA, nB);
+            if (v0) check_cell<T, WHICH>(K, nA, tbad, smax, sbits);
+            if (v1) check_cell<T, WHICH>(K, nB, tbad, smax, sbits);
         }
         if (aborted) break;
         finish_tile<T, VAR, WHICH>(a, t, tile.grid, acc, redo, tbad, smax, sbits, kbad, lane);

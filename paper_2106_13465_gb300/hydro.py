@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "HYDRO_OK", 1: "HYDRO_EINVAL", 2: "HYDRO_ENOMEM", 3: "HYDRO_E
 
 # every symbol the header declares (checked by the CPU test of the ABI)
 EXPORTS = ("hydro_init", "hydro_destroy", "hydro_set_tuning", "hydro_set_wait_limit", "hydro_set_state",
-           "hydro_get_state", "hydro_step", "hydro_step_dt", "hydro_step_profiled", "hydro_cfl_dt", "hydro_get_time",
+           "hydro_get_state", "hydro_set_rows", "hydro_get_rows", "hydro_step", "hydro_step_dt", "hydro_step_profiled", "hydro_cfl_dt", "hydro_get_time",
            "hydro_get_step", "hydro_set_step", "hydro_set_time",
            "hydro_conservation", "hydro_conservation_noalloc", "hydro_get_stats",
            "hydro_last_error", "hydro_version")
@@ -46,12 +46,13 @@ class hydro_params(ctypes.Structure):
 
 class hydro_tuning(ctypes.Structure):
     _fields_ = [("tile_len", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("graph_steps", ctypes.c_int), ("span_len", ctypes.c_int)]
+                ("graph_steps", ctypes.c_int), ("span_len", ctypes.c_int), ("fused", ctypes.c_int)]
 
 
 class hydro_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("riemann_fp64", ctypes.c_longlong),
-                ("status_flags", ctypes.c_uint), ("kernel_launches", ctypes.c_longlong)]
+                ("status_flags", ctypes.c_uint), ("kernel_launches", ctypes.c_longlong),
+                ("wait_site", ctypes.c_int), ("wait_tile", ctypes.c_int)]
 
 
 _lib = None
@@ -81,6 +82,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.hydro_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     L.hydro_set_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
     L.hydro_get_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+    L.hydro_set_rows.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]
+    L.hydro_get_rows.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]
     L.hydro_step.argtypes = [vp, ctypes.c_int, D]
     L.hydro_step_dt.argtypes = [vp, ctypes.c_int, D, D]
     L.hydro_step_profiled.argtypes = [vp, ctypes.c_int, D]
@@ -98,6 +101,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.hydro_version.argtypes = []
     L.hydro_version.restype = ctypes.c_char_p
     for name in ("hydro_init", "hydro_set_tuning", "hydro_set_wait_limit", "hydro_set_state", "hydro_get_state",
+                 "hydro_set_rows", "hydro_get_rows",
                  "hydro_step", "hydro_step_dt", "hydro_step_profiled", "hydro_cfl_dt",
                  "hydro_get_time", "hydro_get_step", "hydro_set_step", "hydro_set_time",
                  "hydro_conservation", "hydro_get_stats"):
@@ -141,6 +145,14 @@ def hydro_set_state(ctx, grid: int, U_ptr: int, on_device: int) -> int:
 
 def hydro_get_state(ctx, grid: int, U_ptr: int, on_device: int) -> int:
     return load().hydro_get_state(ctx, grid, ctypes.c_void_p(U_ptr), on_device)
+
+
+def hydro_set_rows(ctx, grid: int, row0: int, nrows: int, U_ptr: int, on_device: int) -> int:
+    return load().hydro_set_rows(ctx, grid, row0, nrows, ctypes.c_void_p(U_ptr), on_device)
+
+
+def hydro_get_rows(ctx, grid: int, row0: int, nrows: int, U_ptr: int, on_device: int) -> int:
+    return load().hydro_get_rows(ctx, grid, row0, nrows, ctypes.c_void_p(U_ptr), on_device)
 
 
 def hydro_step(ctx, nsteps: int, dt_override: np.ndarray | None = None) -> int:
@@ -256,8 +268,9 @@ class Context:
         self.close()
 
     def set_tuning(self, tile_len: int = 0, ctas_per_sm: int = 0, graph_steps: int = 20,
-                   span_len: int = 0) -> None:
-        self._check(hydro_set_tuning(self.ctx, hydro_tuning(tile_len, ctas_per_sm, graph_steps, span_len)))
+                   span_len: int = 0, fused: int = 0) -> None:
+        self._check(hydro_set_tuning(self.ctx, hydro_tuning(tile_len, ctas_per_sm, graph_steps, span_len,
+                                                            fused)))
 
     def set_wait_limit(self, polls: int = -1) -> None:
         """Polls of a TMA completion before a sweep gives up (-1: default)."""
@@ -280,6 +293,26 @@ class Context:
             return out
         a = np.empty((4, ny, nx)) if out is None else out
         self._check(hydro_get_state(self.ctx, grid, a.ctypes.data, 0))
+        return a
+
+    def set_rows(self, grid: int, row0: int, U) -> None:
+        """Write rows [row0, row0 + U.shape[1]) of a grid (U: [4, nrows, nx])."""
+        if hasattr(U, "data_ptr"):
+            self._check(hydro_set_rows(self.ctx, grid, row0, int(U.shape[1]), U.data_ptr(), 1))
+        else:
+            a = np.ascontiguousarray(U, dtype=np.float64)
+            if a.ndim != 3 or a.shape[0] != 4 or a.shape[2] != self.grids[grid][0]:
+                raise ValueError("rows must be [4, nrows, nx]")
+            self._check(hydro_set_rows(self.ctx, grid, row0, a.shape[1], a.ctypes.data, 0))
+
+    def get_rows(self, grid: int, row0: int, nrows: int, out=None):
+        """Read rows [row0, row0 + nrows) of a grid as [4, nrows, nx]."""
+        nx = self.grids[grid][0]
+        if out is not None and hasattr(out, "data_ptr"):
+            self._check(hydro_get_rows(self.ctx, grid, row0, nrows, out.data_ptr(), 1))
+            return out
+        a = np.empty((4, nrows, nx)) if out is None else out
+        self._check(hydro_get_rows(self.ctx, grid, row0, nrows, a.ctypes.data, 0))
         return a
 
     def step(self, nsteps: int, dt_override=None, record_dt: bool = False):
@@ -332,4 +365,4 @@ class Context:
         st, s = hydro_get_stats(self.ctx)
         self._check(st)
         return {"steps": s.steps, "riemann_fp64": s.riemann_fp64, "status_flags": s.status_flags,
-                "kernel_launches": s.kernel_launches}
+                "kernel_launches": s.kernel_launches, "wait_site": s.wait_site, "wait_tile": s.wait_tile}
