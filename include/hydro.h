@@ -53,6 +53,21 @@ enum { HYDRO_BC_REFLECT = 0, HYDRO_BC_TRANSMISSIVE = 1, HYDRO_BC_PERIODIC = 2 };
 
 enum { HYDRO_PREC_FP32 = 32, HYDRO_PREC_FP64 = 64 };
 
+/* Scheme variants (§1 leaves the details of the scheme to its ref. [5]; the
+ * HYDRO code it studies offers these options).  The defaults (0) are the
+ * method as this library reads §1: the exact Riemann solver and minmod.
+ *   riemann_solver  HYDRO_RIEMANN_EXACT: Newton on the exact pressure
+ *                   function (shock and rarefaction branches);
+ *                   HYDRO_RIEMANN_TWO_SHOCK: Newton on the two-shock
+ *                   approximation (the shock relation for both waves,
+ *                   whatever the sign of p - p_K); the state at x/t = 0 is
+ *                   sampled from the same wave pattern in both.
+ *   slope_type      HYDRO_SLOPE_MINMOD, HYDRO_SLOPE_MC (monotonized central:
+ *                   the smallest of 2a, 2b, (a+b)/2 when a, b share a sign),
+ *                   HYDRO_SLOPE_NONE (no reconstruction: first-order Godunov). */
+enum { HYDRO_RIEMANN_EXACT = 0, HYDRO_RIEMANN_TWO_SHOCK = 1 };
+enum { HYDRO_SLOPE_MINMOD = 0, HYDRO_SLOPE_MC = 1, HYDRO_SLOPE_NONE = 2 };
+
 /* One grid: nx * ny interior cells (each in [2, 2^24], and ny times nx
  * rounded up to a multiple of 32 below 2^31), square cells of side h > 0,
  * boundary conditions bc[] = {x low, x high, y low, y high}. */
@@ -75,7 +90,8 @@ typedef struct {
  *   c_floor        sound-speed floor: p >= rho c_floor^2 / gamma (> 0)
  *   ngrids, grids  the grids this context advances together (>= 1)
  *   cuda_stream    a cudaStream_t to enqueue on, or NULL for a stream the
- *                  context creates and owns */
+ *                  context creates and owns
+ *   riemann_solver, slope_type  scheme variants (above; 0 = the defaults) */
 typedef struct {
     int precision;
     double gamma, cfl;
@@ -84,6 +100,8 @@ typedef struct {
     int ngrids;
     const hydro_grid *grids;
     void *cuda_stream;
+    int riemann_solver;
+    int slope_type;
 } hydro_params;
 
 /* Launch shape of the sweep kernels (0 = library default / automatic).

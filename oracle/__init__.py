@@ -36,6 +36,10 @@ _lib_omp = None
 BC_REFLECT, BC_TRANSMISSIVE, BC_PERIODIC = 0, 1, 2
 
 
+RIEMANN_EXACT, RIEMANN_TWO_SHOCK = 0, 1
+SLOPE_MINMOD, SLOPE_MC, SLOPE_NONE = 0, 1, 2
+
+
 class Params(ctypes.Structure):
     _fields_ = [
         ("gamma", ctypes.c_double),
@@ -43,11 +47,16 @@ class Params(ctypes.Structure):
         ("niter", ctypes.c_int),
         ("rho_floor", ctypes.c_double),
         ("c_floor", ctypes.c_double),
+        ("riemann", ctypes.c_int),
+        ("slope", ctypes.c_int),
     ]
 
 
-def params(gamma=1.4, cfl=0.8, niter=10, rho_floor=1e-10, c_floor=1e-10) -> Params:
-    return Params(gamma, cfl, niter, rho_floor, c_floor)
+def params(gamma=1.4, cfl=0.8, niter=10, rho_floor=1e-10, c_floor=1e-10,
+           riemann=RIEMANN_EXACT, slope=SLOPE_MINMOD) -> Params:
+    """Scheme parameters; riemann (exact / two-shock pressure function) and
+    slope (minmod / monotonized central / none) select the variants."""
+    return Params(gamma, cfl, niter, rho_floor, c_floor, riemann, slope)
 
 
 def build(force: bool = False, omp: bool = False) -> str:

@@ -50,7 +50,18 @@ typedef struct {
     int niter;         /* Newton iterations of the Riemann solver (10) */
     double rho_floor;  /* density floor */
     double c_floor;    /* sound-speed floor: p >= rho c_floor^2 / gamma */
+    int riemann;       /* ORC_RIEMANN_EXACT or ORC_RIEMANN_TWO_SHOCK */
+    int slope;         /* ORC_SLOPE_MINMOD, ORC_SLOPE_MC or ORC_SLOPE_NONE */
 } orc_params;
+
+/* Scheme variants (the HYDRO options the paper leaves to its ref. [5]):
+ * the Riemann solver's pressure function -- exact (shock and rarefaction
+ * branches) or the two-shock approximation (the shock branch on both
+ * sides, whatever the sign of p - p_K) -- and the limited slope of the
+ * MUSCL reconstruction -- minmod, monotonized central, or none (first-order
+ * Godunov).  The defaults are the exact solver and minmod. */
+enum { ORC_RIEMANN_EXACT = 0, ORC_RIEMANN_TWO_SHOCK = 1 };
+enum { ORC_SLOPE_MINMOD = 0, ORC_SLOPE_MC = 1, ORC_SLOPE_NONE = 2 };
 
 enum { ORC_BC_REFLECT = 0, ORC_BC_TRANSMISSIVE = 1, ORC_BC_PERIODIC = 2 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENEGATIVE = 4 };
@@ -124,6 +135,26 @@ static double minmod(double a, double b)
     return 0.0;
 }
 
+/* Monotonized central slope of the one-sided differences a, b: 0 when
+ * their signs differ or either is 0, else the one of smallest magnitude
+ * among 2a, 2b and (a + b)/2, with their common sign. */
+static double mc_slope(double a, double b)
+{
+    if (!((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0))) return 0.0;
+    double c = 0.5 * (a + b);
+    double m = fabs(c);
+    if (fabs(2.0 * a) < m) m = fabs(2.0 * a);
+    if (fabs(2.0 * b) < m) m = fabs(2.0 * b);
+    return (a > 0.0) ? m : -m;
+}
+
+static double limited_slope(const orc_params *P, double a, double b)
+{
+    if (P->slope == ORC_SLOPE_MC) return mc_slope(a, b);
+    if (P->slope == ORC_SLOPE_NONE) return 0.0;
+    return minmod(a, b);
+}
+
 /* Trace of cell i from its primitive neighbours Wm = W_{i-1}, W0 = W_i,
  * Wp = W_{i+1}.  Slopes D = minmod of the one-sided differences of each
  * primitive; half-step predictor dW = -(dt/dx)/2 * A(W_i) D with the
@@ -136,7 +167,7 @@ static void muscl_hancock_trace(const orc_params *P, double dtdx,
                                 const double Wp[4], double WL[4], double WR[4])
 {
     double D[4], dW[4];
-    for (int q = 0; q < 4; q++) D[q] = minmod(W0[q] - Wm[q], Wp[q] - W0[q]);
+    for (int q = 0; q < 4; q++) D[q] = limited_slope(P, W0[q] - Wm[q], Wp[q] - W0[q]);
 
     double rho = W0[0], u = W0[1], p = W0[3];
     double half = -0.5 * dtdx;
@@ -166,12 +197,15 @@ static void muscl_hancock_trace(const orc_params *P, double dtdx,
  *   f' = sqrt(A_K/(p+B_K)) (1 - (p - p_K) / (2 (B_K + p))).
  * Rarefaction branch (p <= p_K):
  *   f = 2 c_K/(gamma-1) ((p/p_K)^((gamma-1)/(2 gamma)) - 1),
- *   f' = (p/p_K)^(-(gamma+1)/(2 gamma)) / (rho_K c_K). */
+ *   f' = (p/p_K)^(-(gamma+1)/(2 gamma)) / (rho_K c_K).
+ * The two-shock approximation takes the shock branch for every p: the
+ * Lagrangian shock speed W_K = sqrt(gamma p_K rho_K (1 + (gamma+1)/(2 gamma)
+ * (p - p_K)/p_K)) of both waves, f = (p - p_K)/W_K (the same expression). */
 static void pressure_function(const orc_params *P, double p, double rk,
                               double pk, double ck, double *f, double *df)
 {
     double g = P->gamma;
-    if (p > pk) {
+    if (p > pk || P->riemann == ORC_RIEMANN_TWO_SHOCK) {
         double A = 2.0 / ((g + 1.0) * rk);
         double B = (g - 1.0) / (g + 1.0) * pk;
         double q = sqrt(A / (p + B));

@@ -46,10 +46,15 @@ struct Consts {
     T tol;        // Newton convergence test |p_new - p| <= tol * p_new
     int niter;    // maximum Newton iterations
     int g75;      // g = 7/5: z = 1/7, G4 = 5, G3 = 7 (a 7th root and integer powers)
+    int two_shock;  // Riemann solver variant: the two-shock pressure function on both sides
+    int slope;      // slope variant: SLOPE_MINMOD, SLOPE_MC or SLOPE_NONE
     T bz[kBinomTerms];  // binomial coefficients C(z, k), k = 1 .. kBinomTerms
     T pz_series;        // (1 - kBinomRadius)^z: (p/p_K)^z below it came from exp2/log2
     float f_gamma, f_gm1, f_rho_floor, f_cf2g;  // FP32 copies (the FP64 CFL estimate)
 };
+
+// Scheme variants (the HYDRO options the paper leaves to its ref. [5]).
+enum { SLOPE_MINMOD = 0, SLOPE_MC = 1, SLOPE_NONE = 2 };
 
 template <class T> struct Prim { T r, u, v, p; };     // u normal, v tangential
 template <class T> struct Cons { T r, mn, mt, E; };   // (rho, m_n, m_t, E)
@@ -246,6 +251,38 @@ __device__ __forceinline__ float minmod(float a, float b) {
     return (a * b > 0.0f) ? ((fabsf(a) < fabsf(b)) ? a : b) : 0.0f;
 }
 
+// Monotonized central slope: 0 unless a and b are both > 0 or both < 0,
+// then the one of 2a, 2b and (a + b)/2 of smallest magnitude (ties go to
+// the earlier of (a + b)/2, 2a, 2b: the values are then equal).  FP64
+// compares the magnitudes on the integer pipe, as minmod does.
+__device__ __forceinline__ double mc_slope(double a, double b) {
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    if (!(((ia ^ ib) >= 0) && ((ia << 1) != 0) && ((ib << 1) != 0))) return 0.0;
+    const double c = 0.5 * (a + b), a2 = 2.0 * a, b2 = 2.0 * b;
+    unsigned long long m = (unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffull;
+    const unsigned long long ma = (unsigned long long)__double_as_longlong(a2) & 0x7fffffffffffffffull;
+    const unsigned long long mb = (unsigned long long)__double_as_longlong(b2) & 0x7fffffffffffffffull;
+    m = (ma < m) ? ma : m;
+    m = (mb < m) ? mb : m;
+    return __longlong_as_double((long long)m | (ia & (long long)0x8000000000000000ull));
+}
+__device__ __forceinline__ float mc_slope(float a, float b) {
+    if (!(a * b > 0.0f)) return 0.0f;
+    const float c = 0.5f * (a + b);
+    float m = fabsf(c);
+    m = (fabsf(2.0f * a) < m) ? fabsf(2.0f * a) : m;
+    m = (fabsf(2.0f * b) < m) ? fabsf(2.0f * b) : m;
+    return (a > 0.0f) ? m : -m;
+}
+
+// The limited slope of the one-sided differences a, b (the variant of K).
+template <class T>
+__device__ __forceinline__ T limited_slope(const Consts<T>& K, T a, T b) {
+    if (K.slope == SLOPE_MINMOD) return minmod(a, b);
+    if (K.slope == SLOPE_MC) return mc_slope(a, b);
+    return T(0);
+}
+
 // Exact shortcuts for states equal bit for bit, per arithmetic type: the
 // trace between equal neighbours (trace), the Riemann problem of equal states
 // (equal_state_flux) and, in the sweeps, uniform 5-point stencils (a cell
@@ -317,10 +354,18 @@ __device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) *
         WR = W0;
         return;
     }
-    const T Dr = minmod(W0.r - Wm.r, Wp.r - W0.r);
-    const T Du = minmod(W0.u - Wm.u, Wp.u - W0.u);
-    const T Dv = minmod(W0.v - Wm.v, Wp.v - W0.v);
-    const T Dp = minmod(W0.p - Wm.p, Wp.p - W0.p);
+    T Dr, Du, Dv, Dp;
+    if (K.slope == SLOPE_MINMOD) {  // the default, without the variant's test per slope
+        Dr = minmod(W0.r - Wm.r, Wp.r - W0.r);
+        Du = minmod(W0.u - Wm.u, Wp.u - W0.u);
+        Dv = minmod(W0.v - Wm.v, Wp.v - W0.v);
+        Dp = minmod(W0.p - Wm.p, Wp.p - W0.p);
+    } else {
+        Dr = limited_slope(K, W0.r - Wm.r, Wp.r - W0.r);
+        Du = limited_slope(K, W0.u - Wm.u, Wp.u - W0.u);
+        Dv = limited_slope(K, W0.v - Wm.v, Wp.v - W0.v);
+        Dp = limited_slope(K, W0.p - Wm.p, Wp.p - W0.p);
+    }
     const T dr = hdtdx * tfma(W0.u, Dr, W0.r * Du);
     const T du = hdtdx * tfma(W0.u, Du, Dp * ir0);
     const T dv = hdtdx * (W0.u * Dv);
@@ -388,11 +433,13 @@ __device__ __forceinline__ Side<T> make_side(const Consts<T>& K, const Prim<T>& 
 }
 
 // f_K(p) with f_K' = a/p + b; pz = (p/p_K)^z on the rarefaction branch, -1 on
-// the shock branch.  p == p_K gives f = 0 and pz = 1 exactly.
+// the shock branch.  p == p_K gives f = 0 and pz = 1 exactly.  The
+// two-shock variant takes the shock branch for every p (the Lagrangian
+// shock speed of both waves, f = (p - p_K)/W_K(p), the same expression).
 template <class T>
 __device__ __forceinline__ void pressure_fn(const Consts<T>& K, const Side<T>& s, T p,
                                             T& f, T& a, T& b, T& pz) {
-    if (gt_pos(p, s.p)) {
+    if (gt_pos(p, s.p) || K.two_shock) {
         const T q = trsqrt((p + s.B) * s.iA);
         const T dpk = p - s.p;
         f = dpk * q;

@@ -53,6 +53,8 @@ Consts<T> make_consts(const hydro_params& p, double tol) {
     K.tol = (T)tol;
     K.niter = p.niter_riemann;
     K.g75 = (g == 1.4) ? 1 : 0;
+    K.two_shock = p.riemann_solver == HYDRO_RIEMANN_TWO_SHOCK ? 1 : 0;
+    K.slope = p.slope_type == HYDRO_SLOPE_MC ? SLOPE_MC : (p.slope_type == HYDRO_SLOPE_NONE ? SLOPE_NONE : SLOPE_MINMOD);
     double c = 1.0, z = (g - 1.0) / (2.0 * g);
     for (int k = 1; k <= kBinomTerms; ++k) {
         c *= (z - (k - 1)) / k;  // C(z, k)
@@ -162,6 +164,10 @@ hydro_status validate_params(const hydro_params* p) {
         return fail(nullptr, HYDRO_EINVAL, "niter_riemann must be in [0, 1000]");
     if (!(p->rho_floor > 0.0) || !(p->c_floor > 0.0))
         return fail(nullptr, HYDRO_EINVAL, "rho_floor and c_floor must be > 0");
+    if (p->riemann_solver != HYDRO_RIEMANN_EXACT && p->riemann_solver != HYDRO_RIEMANN_TWO_SHOCK)
+        return fail(nullptr, HYDRO_EINVAL, "riemann_solver must be HYDRO_RIEMANN_EXACT or HYDRO_RIEMANN_TWO_SHOCK");
+    if (p->slope_type < HYDRO_SLOPE_MINMOD || p->slope_type > HYDRO_SLOPE_NONE)
+        return fail(nullptr, HYDRO_EINVAL, "slope_type must be HYDRO_SLOPE_MINMOD, _MC or _NONE");
     if (p->ngrids < 1 || !p->grids)
         return fail(nullptr, HYDRO_EINVAL, "need ngrids >= 1 and a grids array");
     for (int g = 0; g < p->ngrids; ++g) {

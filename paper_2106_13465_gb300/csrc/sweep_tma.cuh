@@ -418,7 +418,7 @@ __device__ __forceinline__ Cons<T> update(const Cons<T>& u, T dtdx, const Cons<T
 template <class T, int VAR, int DIR>
 struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_Y> { static constexpr int value = 5; };
-template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_X> { static constexpr int value = 6; };
+template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_X> { static constexpr int value = 7; };
 template <> struct MinBlocks<double, VAR_F64, DIR_Y> { static constexpr int value = 3; };
 template <> struct MinBlocks<double, VAR_F64, DIR_X> { static constexpr int value = 3; };
 

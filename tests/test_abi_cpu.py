@@ -79,3 +79,11 @@ def test_no_gpu_reports_cuda_error_not_a_fallback():
     st, ctx = H.hydro_init(p)
     assert st == H.HYDRO_ECUDA
     assert not ctx.value
+
+
+@pytest.mark.parametrize("kw,msg", [(dict(riemann=2), "riemann_solver"), (dict(slope=3), "slope_type")])
+def test_invalid_scheme_variants_rejected(kw, msg):
+    p, _arr = _params(**kw)
+    st, ctx = H.hydro_init(p)
+    assert st == H.HYDRO_EINVAL
+    assert msg in H.hydro_last_error(None)

@@ -11,7 +11,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "hydro_oracle.c")
 PINS = [os.path.join(ROOT, "tests", "test_oracle_riemann.py"),
-        os.path.join(ROOT, "tests", "test_oracle_scheme.py")]
+        os.path.join(ROOT, "tests", "test_oracle_scheme.py"),
+        os.path.join(ROOT, "tests", "test_oracle_variants.py")]
 
 MUTANTS = {
     "trace_drops_pressure_gradient": ("dW[1] = half * (u * D[1] + D[3] / rho);",
@@ -53,6 +54,11 @@ MUTANTS = {
     "density_floor_ignored": ("return (rho < P->rho_floor) ? P->rho_floor : rho;", "return rho;"),
     "riemann_floor_drops_gamma": ("return P->rho_floor * P->c_floor * P->c_floor / P->gamma;",
                                   "return P->rho_floor * P->c_floor * P->c_floor;"),
+    "two_shock_flag_ignored": ("if (p > pk || P->riemann == ORC_RIEMANN_TWO_SHOCK) {", "if (p > pk) {"),
+    "mc_without_central": ("    if (fabs(2.0 * a) < m) m = fabs(2.0 * a);\n",
+                           "    m = fabs(2.0 * a);\n"),
+    "mc_sign_lost": ("    return (a > 0.0) ? m : -m;", "    return m;"),
+    "no_slope_is_minmod": ("    if (P->slope == ORC_SLOPE_NONE) return 0.0;\n", ""),
 }
 
 
