@@ -115,7 +115,7 @@ struct FusedAcc {
 // Sweep box row r (grid row y) along x, the lanes mapped on the segment as
 // in the split x sweep (XMap).  OUT_GLOBAL: to the destination buffer (the
 // second sweep, with the CFL speed), else in place into the box.
-template <class T, int VAR, bool OUT_GLOBAL>
+template <class T, int VAR, bool SV, bool OUT_GLOBAL>
 __device__ __forceinline__ void fused_x_row(const SweepArgs<T>& a, T* box, int r, int y, const GridDesc& g, int bx,
                                             T dtdx, T hdtdx, int lane, FusedAcc<T>& acc, unsigned& nfb) {
     const int n = g.nx;
@@ -132,7 +132,7 @@ __device__ __forceinline__ void fused_x_row(const SweepArgs<T>& a, T* box, int r
     __syncwarp();  // every lane has read before any writes back in place
     bool r0 = false, r1 = false;
     Cons<T> nA, nB;
-    segment_update<T, VAR>(a, dtdx, hdtdx, lane, uA, uB, nA, nB, r0, r1, nfb);
+    segment_update<T, VAR, SV>(a, dtdx, hdtdx, lane, uA, uB, nA, nB, r0, r1, nfb);
     acc.redo |= segment_redo<T>(lane, bx, n, r0, r1);
     const bool v0 = seg_result(P0, bx, n), v1 = seg_result(P1, bx, n);
     if (OUT_GLOBAL) {
@@ -157,7 +157,7 @@ __device__ __forceinline__ void fused_x_row(const SweepArgs<T>& a, T* box, int r
 // barrier (every thread calls this once per sweep), since the walker of the
 // neighbouring rows may overwrite them in place.  `active`: the column is
 // swept (else the thread only joins the barrier).
-template <class T, int VAR, bool OUT_GLOBAL>
+template <class T, int VAR, bool SV, bool OUT_GLOBAL>
 __device__ __forceinline__ void fused_y_col(const SweepArgs<T>& a, T* box, int c, int x, const GridDesc& g, int by,
                                             int s0, int s1, bool active, T dtdx, T hdtdx, FusedAcc<T>& acc,
                                             unsigned& nfb) {
@@ -190,10 +190,10 @@ __device__ __forceinline__ void fused_y_col(const SweepArgs<T>& a, T* box, int c
         T ir2;
         const Prim<T> w2 = cons_to_prim(K, u, ir2);
         Prim<T> wl1, wr1;
-        trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
+        trace<T, SV>(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
         if (k == s0) w.wr0 = wl1;  // the face left of cell s0-1 is not formed: a throw-away problem
         bool rd = false;
-        const Cons<T> fhi = FluxOp<T, VAR>::eval(a, w.wr0, wl1, rd, nfb, wk);  // (k-1) - 1/2
+        const Cons<T> fhi = FluxOp<T, VAR, SV>::eval(a, w.wr0, wl1, rd, nfb, wk);  // (k-1) - 1/2
         if (k >= s0 + 1) acc.redo |= rd;
         if (k >= s0 + 2) {
             const Cons<T> out = update(w.u0, dtdx, fhi, w.flo);  // row k - 2
@@ -224,7 +224,7 @@ struct FusedMinBlocks { static constexpr int value = 1; };
 template <> struct FusedMinBlocks<float, VAR_F32_MAIN> { static constexpr int value = 5; };
 template <> struct FusedMinBlocks<double, VAR_F64> { static constexpr int value = 3; };
 
-template <class T, int VAR, int ORDER>
+template <class T, int VAR, int ORDER, bool SV>
 __global__ void __launch_bounds__(kFusedThreads, (FusedMinBlocks<T, VAR>::value))
     fused_step_kernel(const SweepArgs<T> a) {
     constexpr int NW = kFusedThreads / 32;
@@ -304,24 +304,24 @@ __global__ void __launch_bounds__(kFusedThreads, (FusedMinBlocks<T, VAR>::value)
             for (int r = warp; r < rows + 4; r += NW) {
                 const int y = by + r;
                 const bool need = (y >= 0 && y < g.ny) || (g.bc[2] == BC_PERIODIC && y >= -2 && y <= g.ny + 1);
-                if (need) fused_x_row<T, VAR, false>(a, box, r, y, g, bx, dtdx, hdtdx, lane, acc, nfb);
+                if (need) fused_x_row<T, VAR, SV, false>(a, box, r, y, g, bx, dtdx, hdtdx, lane, acc, nfb);
             }
             __syncthreads();
             // 2. y along the tile's columns (box columns 2 .. 61), to dst
             const int c = 2 + 32 * (warp & 1) + lane;
             const int x = bx + c;
-            fused_y_col<T, VAR, true>(a, box, c, x, g, by, ys0, ys1, c < 62 && x >= 0 && x < g.nx, dtdx, hdtdx,
+            fused_y_col<T, VAR, SV, true>(a, box, c, x, g, by, ys0, ys1, c < 62 && x >= 0 && x < g.nx, dtdx, hdtdx,
                                       acc, nfb);
         } else {
             // 1. y along the box columns the x sweep reads, in place
             const int c = 32 * (warp & 1) + lane;
             const int x = bx + c;
             const bool need = (x >= 0 && x < g.nx) || (g.bc[0] == BC_PERIODIC && x >= -2 && x <= g.nx + 1);
-            fused_y_col<T, VAR, false>(a, box, c, x, g, by, ys0, ys1, need, dtdx, hdtdx, acc, nfb);
+            fused_y_col<T, VAR, SV, false>(a, box, c, x, g, by, ys0, ys1, need, dtdx, hdtdx, acc, nfb);
             __syncthreads();
             // 2. x along the tile's rows (box rows 2 .. rows+1), to dst
             for (int r = 2 + warp; r < rows + 2; r += NW)
-                fused_x_row<T, VAR, true>(a, box, r, by + r, g, bx, dtdx, hdtdx, lane, acc, nfb);
+                fused_x_row<T, VAR, SV, true>(a, box, r, by + r, g, bx, dtdx, hdtdx, lane, acc, nfb);
         }
 
         // end of the tile (the barrier also keeps the box until every thread is done)
@@ -367,8 +367,14 @@ __global__ void __launch_bounds__(kFusedThreads, (FusedMinBlocks<T, VAR>::value)
 template <class T, int VAR>
 cudaError_t launch_fused_var(int order, const SweepArgs<T>& a, int nctas, cudaStream_t s) {
     constexpr int smem = fused_smem_bytes<T>();
-    if (order == 0) fused_step_kernel<T, VAR, 0><<<nctas, kFusedThreads, smem, s>>>(a);
-    else fused_step_kernel<T, VAR, 1><<<nctas, kFusedThreads, smem, s>>>(a);
+    const bool sv = scheme_variant(a.K);
+    if (order == 0) {
+        if (sv) fused_step_kernel<T, VAR, 0, true><<<nctas, kFusedThreads, smem, s>>>(a);
+        else fused_step_kernel<T, VAR, 0, false><<<nctas, kFusedThreads, smem, s>>>(a);
+    } else {
+        if (sv) fused_step_kernel<T, VAR, 1, true><<<nctas, kFusedThreads, smem, s>>>(a);
+        else fused_step_kernel<T, VAR, 1, false><<<nctas, kFusedThreads, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -376,7 +382,8 @@ template <class T, int VAR>
 int fused_occupancy() {
     constexpr int smem = fused_smem_bytes<T>();
     int best = 1 << 30;
-    for (auto fn : {fused_step_kernel<T, VAR, 0>, fused_step_kernel<T, VAR, 1>}) {
+    for (auto fn : {fused_step_kernel<T, VAR, 0, false>, fused_step_kernel<T, VAR, 1, false>,
+                    fused_step_kernel<T, VAR, 0, true>, fused_step_kernel<T, VAR, 1, true>}) {
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
         int nb = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kFusedThreads, smem) != cudaSuccess) return 0;

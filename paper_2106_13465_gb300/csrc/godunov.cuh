@@ -48,6 +48,9 @@ struct Consts {
     int g75;      // g = 7/5: z = 1/7, G4 = 5, G3 = 7 (a 7th root and integer powers)
     int two_shock;  // Riemann solver variant: the two-shock pressure function on both sides
     int slope;      // slope variant: SLOPE_MINMOD, SLOPE_MC or SLOPE_NONE
+                    // (both read only by code compiled with SV = true: the kernels
+                    // are instantiated once for the defaults, with no test of these
+                    // flags, and once for any variant)
     T bz[kBinomTerms];  // binomial coefficients C(z, k), k = 1 .. kBinomTerms
     T pz_series;        // (1 - kBinomRadius)^z: (p/p_K)^z below it came from exp2/log2
     float f_gamma, f_gm1, f_rho_floor, f_cf2g;  // FP32 copies (the FP64 CFL estimate)
@@ -345,7 +348,7 @@ __device__ __forceinline__ bool positive(float x) {
 // Between two neighbours equal to it (bit for bit) every slope is 0, the
 // predictor is -0 and each face equals W0 exactly (W0 is already floored):
 // that case returns W0 without the arithmetic.
-template <class T>
+template <class T, bool SV = false>
 __device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) */,
                                       const Prim<T>& Wm, const Prim<T>& W0, T ir0 /* 1/rho_0 */,
                                       const Prim<T>& Wp, Prim<T>& WL, Prim<T>& WR) {
@@ -355,7 +358,7 @@ __device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) *
         return;
     }
     T Dr, Du, Dv, Dp;
-    if (K.slope == SLOPE_MINMOD) {  // the default, without the variant's test per slope
+    if (!SV || K.slope == SLOPE_MINMOD) {
         Dr = minmod(W0.r - Wm.r, Wp.r - W0.r);
         Du = minmod(W0.u - Wm.u, Wp.u - W0.u);
         Dv = minmod(W0.v - Wm.v, Wp.v - W0.v);
@@ -436,10 +439,10 @@ __device__ __forceinline__ Side<T> make_side(const Consts<T>& K, const Prim<T>& 
 // the shock branch.  p == p_K gives f = 0 and pz = 1 exactly.  The
 // two-shock variant takes the shock branch for every p (the Lagrangian
 // shock speed of both waves, f = (p - p_K)/W_K(p), the same expression).
-template <class T>
+template <class T, bool SV = false>
 __device__ __forceinline__ void pressure_fn(const Consts<T>& K, const Side<T>& s, T p,
                                             T& f, T& a, T& b, T& pz) {
-    if (gt_pos(p, s.p) || K.two_shock) {
+    if (gt_pos(p, s.p) || (SV && K.two_shock)) {
         const T q = trsqrt((p + s.B) * s.iA);
         const T dpk = p - s.p;
         f = dpk * q;
@@ -474,7 +477,7 @@ struct Star {
 // follow from their values at the previous one by a first-order update (the
 // neglected term is of the same order).  Without convergence f_K is
 // evaluated again at the last iterate.  u* = (uL+uR)/2 + (f_R(p*) - f_L(p*))/2.
-template <class T>
+template <class T, bool SV = false>
 __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T>& L,
                                                 const Side<T>& R) {
     T p = tfma(T(-0.125) * (R.u - L.u), (L.r + R.r) * (L.c + R.c), T(0.5) * (L.p + R.p));
@@ -485,8 +488,8 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
     bool conv = false;
     int iters = K.niter + 1;
     for (int it = 0; it < K.niter; ++it) {
-        pressure_fn(K, L, p, fl, al, bl, pzl);
-        pressure_fn(K, R, p, fr, ar, br, pzr);
+        pressure_fn<T, SV>(K, L, p, fl, al, bl, pzl);
+        pressure_fn<T, SV>(K, R, p, fr, ar, br, pzr);
         const T F = fl + fr + du;
         // Newton step / p (F == 0: p is the root, the step is exactly 0)
         const T g = is_zero(F) ? T(0) : tdiv(F, tfma(p, bl + br, al + ar));
@@ -509,8 +512,8 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
         p = pn;
     }
     if (!conv) {
-        pressure_fn(K, L, p, fl, al, bl, pzl);
-        pressure_fn(K, R, p, fr, ar, br, pzr);
+        pressure_fn<T, SV>(K, L, p, fl, al, bl, pzl);
+        pressure_fn<T, SV>(K, R, p, fr, ar, br, pzr);
     }
     Star<T> st;
     st.p = p;
@@ -539,8 +542,14 @@ __device__ __forceinline__ Prim<T> sample_side(const Consts<T>& K, const Side<T>
     const bool one = eq_pos(st.p, S.p);
     const T pr = one ? T(1) : st.p * S.ip;
     if (gt_pos(st.p, S.p)) {
-        const T sk = tfma(-S.c, tsqrt(tfma(K.zs, pr, K.z)), sgn * S.u);   // = sgn * S_K
-        if (ge_zero(sk)) { W.r = S.r; W.u = S.u; W.p = S.p; }
+        // sgn S_K = m - c_K sqrt(zs pr + z) with m = sgn u_K: it is >= 0 (the
+        // shock moves away from x/t = 0 and the side's own state is sampled)
+        // exactly when m >= 0 and m^2 >= c_K^2 (zs pr + z), which needs no
+        // square root.  At a tie the two forms may round apart, but the flux
+        // is continuous across a stationary shock (Rankine-Hugoniot with
+        // zero speed), so either choice gives the same flux to rounding.
+        const T m = sgn * S.u;
+        if (ge_zero(m) && !gt_pos(S.c * S.c * tfma(K.zs, pr, K.z), m * m)) { W.r = S.r; W.u = S.u; W.p = S.p; }
         else { W.r = tdiv(S.r * (pr + K.G6), tfma(K.G6, pr, T(1))); W.u = st.u; W.p = st.p; }
     } else {
         const T hk = sgn * S.u - S.c;                              // head
@@ -622,7 +631,7 @@ __device__ __forceinline__ Cons<T> equal_state_flux(const Consts<T>& K, Prim<T> 
 }
 
 // Godunov flux at one interface between the traced states L | R.
-template <class T>
+template <class T, bool SV = false>
 __device__ __forceinline__ Cons<T> godunov_flux_exact(const Consts<T>& K, const Prim<T>& WL,
                                                       const Prim<T>& WR, bool* floored,
                                                       unsigned* work = nullptr) {
@@ -632,7 +641,7 @@ __device__ __forceinline__ Cons<T> godunov_flux_exact(const Consts<T>& K, const 
         return equal_state_flux(K, WL);
     }
     const Side<T> L = make_side(K, WL), R = make_side(K, WR);
-    const Star<T> s = riemann_star(K, L, R);
+    const Star<T> s = riemann_star<T, SV>(K, L, R);
     if (floored) *floored = s.floored;
     if (work) *work = solve_work(K, s);
     return physical_flux(K, sample0(K, L, R, s));

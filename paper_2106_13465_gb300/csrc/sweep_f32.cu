@@ -8,7 +8,7 @@ namespace hydro {
 
 __device__ __noinline__ Cons<double> flux_fp64_near_vacuum(const Consts<double>* Kd, Prim<double> L,
                                                            Prim<double> R) {
-    return godunov_flux_exact(*Kd, L, R, nullptr);
+    return godunov_flux_exact<double, true>(*Kd, L, R, nullptr);  // the variants read at run time
 }
 
 template <>

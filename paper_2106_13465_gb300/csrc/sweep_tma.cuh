@@ -74,6 +74,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // At most `limit` polls and about kWaitNs nanoseconds (a poll may suspend
 // the thread for a while), whichever comes first.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit = kWaitLimit) {
+    if (limit && mbar_try_wait(bar, parity)) return true;  // the usual case: no timer read
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
@@ -108,16 +109,17 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 // --------------------------------------------------------- interface flux --
-template <class T, int VAR>
+// SV: the scheme variants of a.K are read (else the defaults are compiled in).
+template <class T, int VAR, bool SV>
 struct FluxOp;
 
-template <>
-struct FluxOp<double, VAR_F64> {
+template <bool SV>
+struct FluxOp<double, VAR_F64, SV> {
     static __device__ __forceinline__ Cons<double> eval(const SweepArgs<double>& a, const Prim<double>& L,
                                                         const Prim<double>& R, bool& redo, unsigned& nfb,
                                                         unsigned& work) {
         (void)redo; (void)nfb;
-        return godunov_flux_exact(a.K, L, R, nullptr, &work);
+        return godunov_flux_exact<double, SV>(a.K, L, R, nullptr, &work);
     }
 };
 
@@ -133,15 +135,15 @@ __device__ __forceinline__ bool near_vacuum_f32(const Prim<float>& L, const Prim
 
 // FP32 main pass: the FP32 solve; a near-vacuum interface marks its tile for
 // the second pass (its provisional result is overwritten there).
-template <>
-struct FluxOp<float, VAR_F32_MAIN> {
+template <bool SV>
+struct FluxOp<float, VAR_F32_MAIN, SV> {
     static __device__ __forceinline__ Cons<float> eval(const SweepArgs<float>& a, const Prim<float>& L,
                                                        const Prim<float>& R, bool& redo, unsigned& nfb,
                                                        unsigned& work) {
         (void)nfb; (void)work;
         if (Shortcuts<float>::flux && same_bits(L, R)) return equal_state_flux(a.K, L);  // no solve, no FP64
         const Side<float> SL = make_side(a.K, L), SR = make_side(a.K, R);
-        const Star<float> s = riemann_star(a.K, SL, SR);
+        const Star<float> s = riemann_star<float, SV>(a.K, SL, SR);
         if (near_vacuum_f32(L, R, s)) redo = true;
         return physical_flux(a.K, sample0(a.K, SL, SR, s));
     }
@@ -152,15 +154,15 @@ __device__ __noinline__ Cons<double> flux_fp64_near_vacuum(const Consts<double>*
 
 // FP32 second pass: the same FP32 solve, and the FP64 solve where the
 // near-vacuum criterion holds.
-template <>
-struct FluxOp<float, VAR_F32_REDO> {
+template <bool SV>
+struct FluxOp<float, VAR_F32_REDO, SV> {
     static __device__ __forceinline__ Cons<float> eval(const SweepArgs<float>& a, const Prim<float>& L,
                                                        const Prim<float>& R, bool& redo, unsigned& nfb,
                                                        unsigned& work) {
         (void)redo; (void)work;
         if (Shortcuts<float>::flux && same_bits(L, R)) return equal_state_flux(a.K, L);
         const Side<float> SL = make_side(a.K, L), SR = make_side(a.K, R);
-        const Star<float> s = riemann_star(a.K, SL, SR);
+        const Star<float> s = riemann_star<float, SV>(a.K, SL, SR);
         if (near_vacuum_f32(L, R, s)) {
             ++nfb;
             const Prim<double> Ld = {L.r, L.u, L.v, L.p}, Rd = {R.r, R.u, R.v, R.p};
@@ -463,7 +465,7 @@ __device__ __forceinline__ Cons<T> y_ghost(const T* __restrict__ src, const Grid
     return gsave;
 }
 
-template <class T, int VAR, int WHICH>
+template <class T, int VAR, int WHICH, bool SV>
 __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::value))
     sweep_y_kernel(const SweepArgs<T> a) {
     constexpr int C = 4;
@@ -611,11 +613,11 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                         w2 = cons_to_prim(K, u, ir2);
                     }
                     Prim<T> wl1;
-                    trace(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
+                    trace<T, SV>(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
                     // at k = s0 the face left of cell s0-1 is not formed: solve
                     // a trivial problem (equal states) whose flux is never used
                     if (k == s0) w.wr0 = wl1;
-                    fhi = FluxOp<T, VAR>::eval(a, w.wr0, wl1, redo, nfb, wk);
+                    fhi = FluxOp<T, VAR, SV>::eval(a, w.wr0, wl1, redo, nfb, wk);
                 }
                 // the warp's work at this row is that of its slowest lane
                 if (kRecord) tcost += __reduce_max_sync(0xffffffffu, wk);
@@ -777,7 +779,7 @@ struct XMap {
 // and 31 have no left / right neighbour in the segment and hold no result;
 // they mirror their own cells so their throw-away Riemann problems stay
 // mild and do not stretch the warp's Newton loop.
-template <class T, int VAR>
+template <class T, int VAR, bool SV>
 __device__ __forceinline__ void segment_update(const SweepArgs<T>& a, T dtdx, T hdtdx, int lane,
                                                const Cons<T>& u0, const Cons<T>& u1, Cons<T>& n0,
                                                Cons<T>& n1, bool& r0, bool& r1, unsigned& nfb) {
@@ -791,12 +793,12 @@ __device__ __forceinline__ void segment_update(const SweepArgs<T>& a, T dtdx, T 
     if (lane == 0) Wm = W0;
     if (lane == 31) Wp = W1;
     Prim<T> WLA, WRA, WLB, WRB;
-    trace(K, hdtdx, Wm, W0, ir0, W1, WLA, WRA);  // cell A
-    trace(K, hdtdx, W0, W1, ir1, Wp, WLB, WRB);  // cell B
+    trace<T, SV>(K, hdtdx, Wm, W0, ir0, W1, WLA, WRA);  // cell A
+    trace<T, SV>(K, hdtdx, W0, W1, ir1, Wp, WLB, WRB);  // cell B
     Prim<T> WRm = shfl_up1(WRB);  // right face of A-1
     if (lane == 0) WRm = WLA;
-    const Cons<T> Fm = FluxOp<T, VAR>::eval(a, WRm, WLA, r0, nfb, wk);  // A - 1/2
-    const Cons<T> Fc = FluxOp<T, VAR>::eval(a, WRA, WLB, r1, nfb, wk);  // A + 1/2
+    const Cons<T> Fm = FluxOp<T, VAR, SV>::eval(a, WRm, WLA, r0, nfb, wk);  // A - 1/2
+    const Cons<T> Fc = FluxOp<T, VAR, SV>::eval(a, WRA, WLB, r1, nfb, wk);  // A + 1/2
     const Cons<T> Fp = shfl_down1(Fm);                                 // B + 1/2
     n0 = update(u0, dtdx, Fc, Fm);
     n1 = update(u1, dtdx, Fp, Fc);
@@ -831,7 +833,7 @@ __device__ __forceinline__ void store_seg(T* __restrict__ drow, long long plane,
     if (v0) store_pair<T>(drow + x + 2 * lane, plane, n0, n1, v0, v1);
 }
 
-template <class T, int VAR, int WHICH>
+template <class T, int VAR, int WHICH, bool SV>
 __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::value))
     sweep_x_kernel(const SweepArgs<T> a) {
     constexpr int SEG = kXSegment, STEP = kXStride;
@@ -933,7 +935,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
             }
             bool r0 = false, r1 = false;
             Cons<T> nA, nB;
-            segment_update<T, VAR>(a, dtdx, hdtdx, lane, uA, uB, nA, nB, r0, r1, nfb);
+            segment_update<T, VAR, SV>(a, dtdx, hdtdx, lane, uA, uB, nA, nB, r0, r1, nfb);
             // a second-pass request counts only for interfaces feeding stored cells
             redo |= segment_redo<T>(lane, x, n, r0, r1);
             store_seg<T>(drow, g.plane, lane, x, v0, v1, nA, nB);
@@ -959,28 +961,44 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
 }
 
 // ---------------------------------------------------------------- launch --
-template <class T, int VAR, int WHICH, int DIR>
+template <class T, int VAR, int WHICH, int DIR, bool SV>
 struct KernelOf {
-    static constexpr auto fn() { return DIR == DIR_X ? sweep_x_kernel<T, VAR, WHICH> : sweep_y_kernel<T, VAR, WHICH>; }
+    static constexpr auto fn() {
+        return DIR == DIR_X ? sweep_x_kernel<T, VAR, WHICH, SV> : sweep_y_kernel<T, VAR, WHICH, SV>;
+    }
 };
+
+// Whether the constants select a scheme variant (the kernels compiled with
+// SV = true read the variant flags; the others have the defaults built in).
+template <class T>
+bool scheme_variant(const Consts<T>& K) {
+    return K.two_shock || K.slope != SLOPE_MINMOD;
+}
 
 // Launch (the dynamic shared-memory limit was raised by occupancy_one, which
 // the context calls for every variant it uses before the first launch).
 template <class T, int DIR, int VAR>
 cudaError_t launch_one(const SweepArgs<T>& a, int nctas, cudaStream_t s) {
     constexpr int smem = sweep_smem_bytes<T>(DIR);
-    if (a.which == 0) KernelOf<T, VAR, 0, DIR>::fn()<<<nctas, kSweepThreads, smem, s>>>(a);
-    else KernelOf<T, VAR, 1, DIR>::fn()<<<nctas, kSweepThreads, smem, s>>>(a);
+    const bool sv = scheme_variant(a.K);
+    if (a.which == 0) {
+        if (sv) KernelOf<T, VAR, 0, DIR, true>::fn()<<<nctas, kSweepThreads, smem, s>>>(a);
+        else KernelOf<T, VAR, 0, DIR, false>::fn()<<<nctas, kSweepThreads, smem, s>>>(a);
+    } else {
+        if (sv) KernelOf<T, VAR, 1, DIR, true>::fn()<<<nctas, kSweepThreads, smem, s>>>(a);
+        else KernelOf<T, VAR, 1, DIR, false>::fn()<<<nctas, kSweepThreads, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 // Raise the kernels' dynamic shared-memory limit and return their resident
-// CTAs per SM (the smaller of the two sweep-order instances).
+// CTAs per SM (the smallest over the sweep-order and scheme instances).
 template <class T, int DIR, int VAR>
 int occupancy_one() {
     constexpr int smem = sweep_smem_bytes<T>(DIR);
     int best = 1 << 30;
-    for (auto fn : {KernelOf<T, VAR, 0, DIR>::fn(), KernelOf<T, VAR, 1, DIR>::fn()}) {
+    for (auto fn : {KernelOf<T, VAR, 0, DIR, false>::fn(), KernelOf<T, VAR, 1, DIR, false>::fn(),
+                    KernelOf<T, VAR, 0, DIR, true>::fn(), KernelOf<T, VAR, 1, DIR, true>::fn()}) {
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
         int nb = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kSweepThreads, smem) != cudaSuccess) return 0;
