@@ -198,12 +198,17 @@ hydro_status validate_params(const hydro_params* p) {
 int x_segments(int n) { return (n + 2 + kXStride - 1) / kXStride; }
 
 // Tile work-lists.  y sweep: for each grid, columns in groups of 32 (one per
-// lane), rows in runs of len.  x sweep: for each grid and row, runs of len
-// consecutive segments (one warp task each).
-void build_tiles(const std::vector<GridDesc>& gd, int dir, int len, std::vector<Tile>& out) {
+// lane), rows in runs of len.  x sweep, walking (FP64, xwalk): rows in
+// groups of 32, columns in runs of len.  x sweep in segments (FP32): for each
+// grid and row, runs of len consecutive segments (one warp task each).
+void build_tiles(const std::vector<GridDesc>& gd, int dir, int len, std::vector<Tile>& out, bool xwalk = false) {
     out.clear();
     for (int g = 0; g < (int)gd.size(); ++g) {
-        if (dir == DIR_Y) {
+        if (dir == DIR_X && xwalk) {
+            for (int l0 = 0; l0 < gd[g].ny; l0 += kWarpLines)
+                for (int c0 = 0; c0 < gd[g].nx; c0 += len)
+                    out.push_back(Tile{g, l0, c0, std::min(len, gd[g].nx - c0)});
+        } else if (dir == DIR_Y) {
             for (int l0 = 0; l0 < gd[g].nx; l0 += kWarpLines)
                 for (int c0 = 0; c0 < gd[g].ny; c0 += len)
                     out.push_back(Tile{g, l0, c0, std::min(len, gd[g].ny - c0)});
@@ -227,31 +232,32 @@ void build_fused_tiles(const std::vector<GridDesc>& gd, std::vector<Tile>& out) 
     }
 }
 
-// Cost of a tile in cell units for the scheduling model: y, its cells plus
-// its 4-cell halo; x, the 64 cells of each of its segments plus a start-up.
-double tile_cost(const Tile& t, int dir) {
-    if (dir == DIR_Y) return t.ncell + 4.0;
+// Cost of a tile in cell units for the scheduling model: a walk (y, or x
+// walking), its cells plus its 4-cell halo; x segments, the 64 cells of
+// each of its segments plus a start-up.
+double tile_cost(const Tile& t, int dir, bool xwalk = false) {
+    if (dir == DIR_Y || xwalk) return t.ncell + 4.0;
     return t.ncell * (double)kXSegment + 16.0;
 }
 
 // Makespan of the dynamic tile queue on `warps` resident warps (list
 // scheduling in queue order).
-double list_schedule_makespan(const std::vector<Tile>& tiles, int dir, int warps) {
+double list_schedule_makespan(const std::vector<Tile>& tiles, int dir, int warps, bool xwalk = false) {
     std::vector<double> heap(std::max(1, warps), 0.0);  // min-heap of warp finish times
     std::make_heap(heap.begin(), heap.end(), std::greater<double>());
     double span = 0.0;
     for (const Tile& t : tiles) {
         std::pop_heap(heap.begin(), heap.end(), std::greater<double>());
-        heap.back() += tile_cost(t, dir);
+        heap.back() += tile_cost(t, dir, xwalk);
         span = std::max(span, heap.back());
         std::push_heap(heap.begin(), heap.end(), std::greater<double>());
     }
     return span;
 }
 
-int auto_tile_len(const std::vector<GridDesc>& gd, int dir, int warps) {
+int auto_tile_len(const std::vector<GridDesc>& gd, int dir, int warps, bool xwalk = false) {
     std::vector<int> cand;
-    if (dir == DIR_Y) {
+    if (dir == DIR_Y || xwalk) {
         for (int L = 16; L <= 128; L += 4) cand.push_back(L);
         for (int L : {160, 192, 256, 384, 512}) cand.push_back(L);
     } else {
@@ -261,9 +267,9 @@ int auto_tile_len(const std::vector<GridDesc>& gd, int dir, int warps) {
     double best_span = 1e300;
     std::vector<Tile> t;
     for (int L : cand) {
-        build_tiles(gd, dir, L, t);
+        build_tiles(gd, dir, L, t, xwalk);
         if (t.size() > 4000000) continue;
-        const double span = list_schedule_makespan(t, dir, warps);
+        const double span = list_schedule_makespan(t, dir, warps, xwalk);
         if (span < best_span * 0.999) { best_span = span; best = L; }
     }
     return best;
@@ -288,8 +294,11 @@ hydro_status build_tensor_maps(hydro_ctx* c) {
         for (int b = 0; b < 2; ++b) {
             void* base = (char*)c->buf[b] + (size_t)d.off * c->esz;
             for (int dir = 0; dir < kMapKinds; ++dir) {
-                const cuuint32_t box[3] = {dir == DIR_Y ? 32u : (cuuint32_t)kXSegment,
-                                           dir == DIR_X ? 1u : (dir == DIR_Y ? 4u : (cuuint32_t)kFusedBoxRows), 4u};
+                // x: a segment (FP32) or a chunk of 4 columns x 32 rows (FP64 walks)
+                const bool xw = dir == DIR_X && c->prec == 64;
+                const cuuint32_t box[3] = {dir == DIR_Y ? 32u : (xw ? 4u : (cuuint32_t)kXSegment),
+                                           dir == DIR_X ? (xw ? 32u : 1u) : (dir == DIR_Y ? 4u : (cuuint32_t)kFusedBoxRows),
+                                           4u};
                 CUresult r = encode(&maps[map_index((int)g, b, dir)], dtype, 3, base, dims, strides, box, estr,
                                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -367,10 +376,14 @@ hydro_status upload_tiles(hydro_ctx* c) {
             HCK(c, cudaMemset(c->d_yclaim, 0, sizeof(unsigned long long) * (size_t)c->nyblocks));
         } else {
             if (d == DIR_Y) c->y_adaptive = false;
-            const int L = chosen > 0 ? chosen : auto_tile_len(c->gd, d, resident_warps);
+            // FP64 walks the x lines: span_len (a multiple of 60, so of 4) is
+            // then the cells of a walk
+            const bool xwalk = d == DIR_X && c->prec == 64;
+            const int pick = xwalk ? c->tuning.span_len : chosen;
+            const int L = pick > 0 ? pick : auto_tile_len(c->gd, d, resident_warps, xwalk);
             c->tile_len_used[d] = L;
             std::vector<Tile> t;
-            build_tiles(c->gd, d, L, t);
+            build_tiles(c->gd, d, L, t, xwalk);
             HCK(c, cudaMalloc(&c->d_tiles[d], sizeof(Tile) * t.size()));
             HCK(c, cudaMemcpy(c->d_tiles[d], t.data(), sizeof(Tile) * t.size(), cudaMemcpyHostToDevice));
             c->ntiles[d] = (int)t.size();

@@ -55,10 +55,11 @@ __global__ void __launch_bounds__(256) cfl_refine_kernel(const double* __restric
             }
         };
         if (dir == DIR_X) {
-            // segments cell0 .. cell0 + ncell - 1 of row line0: results [60k - 2, 60k + 58)
-            const int x0 = max(0, kXStride * tile.cell0 - 2);
-            const int x1 = min(g.nx, kXStride * (tile.cell0 + tile.ncell) - 2);
-            for (int x = x0 + lane; x < x1; x += 32) visit(x, tile.line0);
+            // FP64 walks the x lines: rows line0 .. line0 + 31, columns
+            // cell0 .. cell0 + ncell - 1 (a lane per row)
+            const int row = tile.line0 + lane;
+            if (row < g.ny)
+                for (int x = tile.cell0; x < tile.cell0 + tile.ncell; ++x) visit(x, row);
         } else if (dir == DIR_FUSED) {
             // columns [60 line0 - 2, 60 line0 + 58) of rows cell0 .. cell0 + ncell - 1
             const int x0 = max(0, kXStride * tile.line0 - 2);

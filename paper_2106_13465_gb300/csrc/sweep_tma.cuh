@@ -424,11 +424,18 @@ template <> struct MinBlocks<float, VAR_F32_MAIN, DIR_X> { static constexpr int 
 template <> struct MinBlocks<double, VAR_F64, DIR_Y> { static constexpr int value = 3; };
 template <> struct MinBlocks<double, VAR_F64, DIR_X> { static constexpr int value = 3; };
 
-// =================================================================== y ===
-// Lines are columns: lane l walks column line0 + l down a tile of rows
-// [s0, s1), with 4-row chunks (rows s0-2+4c .. s0+1+4c) arriving by TMA.
-// Chunk 0 holds the four warm-up positions s0-2 .. s0+1; every later chunk
-// holds four positions that each complete one output row.
+// ============================================================ line walker ===
+// A lane per line: lane l walks line line0 + l along the cells [s0, s1) of a
+// tile, with chunks of 4 cells of 32 lines (positions s0-2+4c .. s0+1+4c)
+// arriving by TMA.  Chunk 0 holds the four warm-up positions s0-2 .. s0+1;
+// every later chunk holds four positions that each complete one output cell.
+// LD = DIR_Y: the lines are columns (the y sweep, both precisions; chunk box
+// 32 columns x 4 rows).  LD = DIR_X: the lines are rows (the FP64 x sweep;
+// chunk box 4 columns x 32 rows, its x start s0 - 2 + 4c even, as a TMA copy
+// of FP64 needs).  The FP64 x sweep walks rather than taking segments
+// (sweep_x_kernel, which FP32 keeps): no cell is computed twice (a segment
+// computes 64 cells for 60 results) and each warp instruction of the solver
+// serves one interface per lane.
 template <class T>
 struct YWalk {
     Cons<T> u0, u1;   // conserved states at k-2, k-1
@@ -438,26 +445,33 @@ struct YWalk {
     Cons<T> flo;      // flux at (k-2) - 1/2
 };
 
-// this lane's cell j (row kc + j) of a y chunk in shared memory
-template <class T>
+// this lane's cell j (position kc + j) of a chunk in shared memory: y, the
+// box [plane][4 rows][32 columns] (normal momentum plane 2); x, the box
+// [plane][32 rows][4 columns] (normal momentum plane 1)
+template <class T, int LD>
 __device__ __forceinline__ Cons<T> chunk_cell(const T* sp, int j, int lane) {
     constexpr int C = 4;
-    return Cons<T>{sp[(0 * C + j) * 32 + lane], sp[(2 * C + j) * 32 + lane], sp[(1 * C + j) * 32 + lane],
-                   sp[(3 * C + j) * 32 + lane]};
+    if constexpr (LD == DIR_Y)
+        return Cons<T>{sp[(0 * C + j) * 32 + lane], sp[(2 * C + j) * 32 + lane], sp[(1 * C + j) * 32 + lane],
+                       sp[(3 * C + j) * 32 + lane]};
+    else
+        return Cons<T>{sp[(0 * 32 + lane) * C + j], sp[(1 * 32 + lane) * C + j], sp[(2 * 32 + lane) * C + j],
+                       sp[(3 * 32 + lane) * C + j]};
 }
 
-// Boundary cell at row k (k in {-2, -1, n, n+1}) of a y walk.  Reflective /
-// transmissive: the mirror rows 1, 0 are in the first chunk (rows -2..1), the
-// mirror rows n-1, n-2 are the walk's last two conserved states (n-2 is saved
-// when row n is formed); periodic: the wrap-around row from global memory.
-template <class T>
-__device__ __forceinline__ Cons<T> y_ghost(const T* __restrict__ src, const GridDesc& g, int col, int k, int n,
-                                           int bclo, int bchi, const T* sp, int kc, int lane,
-                                           const YWalk<T>& w, Cons<T>& gsave) {
+// Boundary cell at position k (k in {-2, -1, n, n+1}) of a walk.
+// Reflective / transmissive: the mirror cells 1, 0 are in the first chunk
+// (positions -2..1), the mirror cells n-1, n-2 are the walk's last two
+// conserved states (n-2 is saved when position n is formed); periodic: the
+// wrap-around cell from global memory.
+template <class T, int LD>
+__device__ __forceinline__ Cons<T> walk_ghost(const T* __restrict__ src, const GridDesc& g, int line, int k, int n,
+                                              int bclo, int bchi, const T* sp, int kc, int lane,
+                                              const YWalk<T>& w, Cons<T>& gsave) {
     const int bc = (k < 0) ? bclo : bchi;
-    if (bc == BC_PERIODIC) return global_cell<T, DIR_Y>(src, g, col, (k < 0) ? k + n : k - n);
+    if (bc == BC_PERIODIC) return global_cell<T, LD>(src, g, line, (k < 0) ? k + n : k - n);
     const bool f = (bc == BC_REFLECT);
-    if (k < 0) return flip(chunk_cell<T>(sp, -1 - k - kc, lane), f);
+    if (k < 0) return flip(chunk_cell<T, LD>(sp, -1 - k - kc, lane), f);
     if (k == n) {
         gsave = flip(w.u0, f);
         return flip(w.u1, f);
@@ -465,9 +479,9 @@ __device__ __forceinline__ Cons<T> y_ghost(const T* __restrict__ src, const Grid
     return gsave;
 }
 
-template <class T, int VAR, int WHICH, bool SV>
-__global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::value))
-    sweep_y_kernel(const SweepArgs<T> a) {
+template <class T, int VAR, int WHICH, bool SV, int LD>
+__global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
+    sweep_walk_kernel(const SweepArgs<T> a) {
     constexpr int C = 4;
     constexpr int S = ring_slots(DIR_Y);
     constexpr int SLOT = slot_bytes<T>(DIR_Y);
@@ -479,8 +493,8 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
 
     const Consts<T>& K = a.K;
     const unsigned acc = a.ctr->acc;
-    // FP64: every tile records its estimated work for the adaptive y tiles
-    constexpr bool kRecord = (VAR == VAR_F64);
+    // FP64 y: every tile records its estimated work for the adaptive y tiles
+    constexpr bool kRecord = (VAR == VAR_F64) && (LD == DIR_Y);
     unsigned kbad = 0, nfb = 0;
     bool aborted = false;
     // step count of this sweep: the claim word of the adaptive tiles
@@ -499,7 +513,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
         }
         const GridDesc g = a.grids[tile.grid];
         const double dt = a.run[tile.grid].dt;
-        const int n = g.ny, nlines = g.nx;
+        const int n = (LD == DIR_Y) ? g.ny : g.nx, nlines = (LD == DIR_Y) ? g.nx : g.ny;
         if (tile.cell0 < 0 || tile.ncell < 1 || tile.cell0 + tile.ncell > n || tile.line0 < 0 ||
             tile.line0 >= nlines || (tile.line0 & (kWarpLines - 1))) {
             kbad |= STATUS_BAD_TILE;  // never produced by the host or the tiler
@@ -508,23 +522,28 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
         const int line0 = tile.line0, line = line0 + lane;
         const bool valid = line < nlines;
         const int lsafe = valid ? line : nlines - 1;
-        const int bclo = g.bc[2], bchi = g.bc[3];
+        const int bclo = (LD == DIR_Y) ? g.bc[2] : g.bc[0], bchi = (LD == DIR_Y) ? g.bc[3] : g.bc[1];
         const int s0 = tile.cell0, s1 = tile.cell0 + tile.ncell;
         const int kfirst = s0 - 2, klast = s1 + 1;
         const int nch = (klast - kfirst) / C + 1;
-        const CUtensorMap* msrc = a.maps + map_index(tile.grid, a.src_buf, DIR_Y);
+        const CUtensorMap* msrc = a.maps + map_index(tile.grid, a.src_buf, LD);
+        auto issue = [&](int c) {
+            if (LD == DIR_Y) ring.issue(c % S, msrc, line0, kfirst + c * C);
+            else ring.issue(c % S, msrc, kfirst + c * C, line0);
+        };
         if (lane == 0)
-            for (int c = 0; c < S && c < nch; ++c) ring.issue(c, msrc, line0, kfirst + c * C);
+            for (int c = 0; c < S && c < nch; ++c) issue(c);
 
         const T dtdx = T(dt / g.h);
         const T hdtdx = T(-0.5) * dtdx;
-        // this lane's column in the four output planes (normal momentum is
-        // plane 2); a plane holds fewer than 2^31 elements (checked on the host)
-        T* __restrict__ q0 = a.dst + g.off + lsafe;
-        T* __restrict__ qn = q0 + 2 * g.plane;
-        T* __restrict__ qt = q0 + g.plane;
+        // this lane's line in the four output planes (normal momentum is
+        // plane 2 for y, 1 for x), cell k at offset k * kstride; a plane
+        // holds fewer than 2^31 elements (checked on the host)
+        T* __restrict__ q0 = a.dst + g.off + ((LD == DIR_Y) ? (long long)lsafe : (long long)lsafe * g.pitch);
+        T* __restrict__ qn = q0 + ((LD == DIR_Y) ? 2 : 1) * g.plane;
+        T* __restrict__ qt = q0 + ((LD == DIR_Y) ? 1 : 2) * g.plane;
         T* __restrict__ qe = q0 + 3 * g.plane;
-        const unsigned pitch = (unsigned)g.pitch;
+        const unsigned pitch = (LD == DIR_Y) ? (unsigned)g.pitch : 1u;
         YWalk<T> w = {};
         Cons<T> gsave = {};  // mirror of row n-2, kept for position n+1
         int run = 1;         // positions ending at the current one with equal conserved bits
@@ -538,7 +557,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
             const int sl = c % S;
             if (!ring.wait(sl, lane, a.wait_limit)) {
                 aborted = true;
-                if (lane == 0) record_wait_site(a.ctr, 2, t);
+                if (lane == 0) record_wait_site(a.ctr, LD == DIR_Y ? 2 : 1, t);
                 break;
             }
             const T* sp = reinterpret_cast<const T*>(ring.slot(sl));
@@ -547,12 +566,12 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
             if (c == 0) {
                 // positions s0-2 and s0-1 only fill the window (both < n - 1;
                 // below 0 they mirror rows of this chunk or wrap around)
-                Cons<T> u = chunk_cell<T>(sp, 0, lane);
-                if (kc < 0) u = y_ghost<T>(a.src, g, lsafe, kc, n, bclo, bchi, sp, kc, lane, w, gsave);
+                Cons<T> u = chunk_cell<T, LD>(sp, 0, lane);
+                if (kc < 0) u = walk_ghost<T, LD>(a.src, g, lsafe, kc, n, bclo, bchi, sp, kc, lane, w, gsave);
                 w.u0 = u;
                 w.w0 = cons_to_prim(K, u);
-                u = chunk_cell<T>(sp, 1, lane);
-                if (kc + 1 < 0) u = y_ghost<T>(a.src, g, lsafe, kc + 1, n, bclo, bchi, sp, kc, lane, w, gsave);
+                u = chunk_cell<T, LD>(sp, 1, lane);
+                if (kc + 1 < 0) u = walk_ghost<T, LD>(a.src, g, lsafe, kc + 1, n, bclo, bchi, sp, kc, lane, w, gsave);
                 w.u1 = u;
                 w.w1 = cons_to_prim(K, u, w.ir1);
                 run = (Shortcuts<T>::stencil && same_bits(w.u1, w.u0)) ? 2 : 1;
@@ -567,7 +586,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
                 // speed -- do exactly that, for the whole warp at once
                 unsigned long long dif = 0;
 #pragma unroll
-                for (int j = 0; j < C; ++j) dif |= (unsigned long long)diff_bits(chunk_cell<T>(sp, j, lane), w.u1);
+                for (int j = 0; j < C; ++j) dif |= (unsigned long long)diff_bits(chunk_cell<T, LD>(sp, j, lane), w.u1);
                 if (__all_sync(0xffffffffu, !valid || dif == 0)) {
                     if (valid) {
                         const Cons<T> out = w.u0;
@@ -592,8 +611,8 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
             for (int j = j0; j < C; ++j) {
                 const int k = kc + j;
                 if (k > klast) break;
-                Cons<T> u = chunk_cell<T>(sp, j, lane);
-                if (k >= n) u = y_ghost<T>(a.src, g, lsafe, k, n, bclo, bchi, sp, kc, lane, w, gsave);
+                Cons<T> u = chunk_cell<T, LD>(sp, j, lane);
+                if (k >= n) u = walk_ghost<T, LD>(a.src, g, lsafe, k, n, bclo, bchi, sp, kc, lane, w, gsave);
                 const bool same = Shortcuts<T>::stencil && same_bits(u, w.u1);
                 run = same ? run + 1 : 1;
                 // rows k-4..k equal bit for bit: the traces of k-3..k-1 return
@@ -653,7 +672,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_Y>::valu
             __syncwarp();
             if (lane == 0 && c + S < nch) {
                 fence_proxy_async_smem();
-                ring.issue(sl, msrc, line0, kfirst + (c + S) * C);
+                issue(c + S);
             }
         }
         if (aborted) break;
@@ -961,12 +980,23 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, DIR_X>::valu
 }
 
 // ---------------------------------------------------------------- launch --
+// The x sweep walks lines in FP64 and takes segments in FP32.
+template <class T>
+__host__ __device__ constexpr bool x_walks() { return sizeof(T) == 8; }
+
 template <class T, int VAR, int WHICH, int DIR, bool SV>
 struct KernelOf {
     static constexpr auto fn() {
-        return DIR == DIR_X ? sweep_x_kernel<T, VAR, WHICH, SV> : sweep_y_kernel<T, VAR, WHICH, SV>;
+        if constexpr (DIR == DIR_X && !x_walks<T>()) return sweep_x_kernel<T, VAR, WHICH, SV>;
+        else return sweep_walk_kernel<T, VAR, WHICH, SV, DIR>;
     }
 };
+
+// Dynamic shared memory of a sweep launch (a walker's ring holds chunks).
+template <class T, int DIR>
+constexpr int launch_smem_bytes() {
+    return sweep_smem_bytes<T>((DIR == DIR_X && !x_walks<T>()) ? DIR_X : DIR_Y);
+}
 
 // Whether the constants select a scheme variant (the kernels compiled with
 // SV = true read the variant flags; the others have the defaults built in).
@@ -979,7 +1009,7 @@ bool scheme_variant(const Consts<T>& K) {
 // the context calls for every variant it uses before the first launch).
 template <class T, int DIR, int VAR>
 cudaError_t launch_one(const SweepArgs<T>& a, int nctas, cudaStream_t s) {
-    constexpr int smem = sweep_smem_bytes<T>(DIR);
+    constexpr int smem = launch_smem_bytes<T, DIR>();
     const bool sv = scheme_variant(a.K);
     if (a.which == 0) {
         if (sv) KernelOf<T, VAR, 0, DIR, true>::fn()<<<nctas, kSweepThreads, smem, s>>>(a);
@@ -995,7 +1025,7 @@ cudaError_t launch_one(const SweepArgs<T>& a, int nctas, cudaStream_t s) {
 // CTAs per SM (the smallest over the sweep-order and scheme instances).
 template <class T, int DIR, int VAR>
 int occupancy_one() {
-    constexpr int smem = sweep_smem_bytes<T>(DIR);
+    constexpr int smem = launch_smem_bytes<T, DIR>();
     int best = 1 << 30;
     for (auto fn : {KernelOf<T, VAR, 0, DIR, false>::fn(), KernelOf<T, VAR, 1, DIR, false>::fn(),
                     KernelOf<T, VAR, 0, DIR, true>::fn(), KernelOf<T, VAR, 1, DIR, true>::fn()}) {
