@@ -64,9 +64,14 @@ enum { HYDRO_PREC_FP32 = 32, HYDRO_PREC_FP64 = 64 };
  *                   sampled from the same wave pattern in both.
  *   slope_type      HYDRO_SLOPE_MINMOD, HYDRO_SLOPE_MC (monotonized central:
  *                   the smallest of 2a, 2b, (a+b)/2 when a, b share a sign),
- *                   HYDRO_SLOPE_NONE (no reconstruction: first-order Godunov). */
+ *                   HYDRO_SLOPE_NONE (no reconstruction: first-order Godunov).
+ *   trace_type      HYDRO_TRACE_MUSCL_HANCOCK: both faces take the whole
+ *                   half-step predictor; HYDRO_TRACE_CHARACTERISTIC: the slopes
+ *                   are split into the acoustic, entropy and shear waves and
+ *                   each face takes only the waves moving toward it. */
 enum { HYDRO_RIEMANN_EXACT = 0, HYDRO_RIEMANN_TWO_SHOCK = 1 };
 enum { HYDRO_SLOPE_MINMOD = 0, HYDRO_SLOPE_MC = 1, HYDRO_SLOPE_NONE = 2 };
+enum { HYDRO_TRACE_MUSCL_HANCOCK = 0, HYDRO_TRACE_CHARACTERISTIC = 1 };
 
 /* One grid: nx * ny interior cells (each in [2, 2^24], and ny times nx
  * rounded up to a multiple of 32 below 2^31), square cells of side h > 0,
@@ -91,7 +96,8 @@ typedef struct {
  *   ngrids, grids  the grids this context advances together (>= 1)
  *   cuda_stream    a cudaStream_t to enqueue on, or NULL for a stream the
  *                  context creates and owns
- *   riemann_solver, slope_type  scheme variants (above; 0 = the defaults) */
+ *   riemann_solver, slope_type, trace_type  scheme variants (above; 0 = the
+ *                  defaults) */
 typedef struct {
     int precision;
     double gamma, cfl;
@@ -102,6 +108,7 @@ typedef struct {
     void *cuda_stream;
     int riemann_solver;
     int slope_type;
+    int trace_type;
 } hydro_params;
 
 /* Launch shape of the sweep kernels (0 = library default / automatic).

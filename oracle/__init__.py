@@ -38,6 +38,7 @@ BC_REFLECT, BC_TRANSMISSIVE, BC_PERIODIC = 0, 1, 2
 
 RIEMANN_EXACT, RIEMANN_TWO_SHOCK = 0, 1
 SLOPE_MINMOD, SLOPE_MC, SLOPE_NONE = 0, 1, 2
+TRACE_MUSCL_HANCOCK, TRACE_CHARACTERISTIC = 0, 1
 
 
 class Params(ctypes.Structure):
@@ -49,14 +50,16 @@ class Params(ctypes.Structure):
         ("c_floor", ctypes.c_double),
         ("riemann", ctypes.c_int),
         ("slope", ctypes.c_int),
+        ("trace", ctypes.c_int),
     ]
 
 
 def params(gamma=1.4, cfl=0.8, niter=10, rho_floor=1e-10, c_floor=1e-10,
-           riemann=RIEMANN_EXACT, slope=SLOPE_MINMOD) -> Params:
-    """Scheme parameters; riemann (exact / two-shock pressure function) and
-    slope (minmod / monotonized central / none) select the variants."""
-    return Params(gamma, cfl, niter, rho_floor, c_floor, riemann, slope)
+           riemann=RIEMANN_EXACT, slope=SLOPE_MINMOD, trace=TRACE_MUSCL_HANCOCK) -> Params:
+    """Scheme parameters; riemann (exact / two-shock pressure function),
+    slope (minmod / monotonized central / none) and trace (MUSCL-Hancock /
+    characteristic tracing) select the variants."""
+    return Params(gamma, cfl, niter, rho_floor, c_floor, riemann, slope, trace)
 
 
 def build(force: bool = False, omp: bool = False) -> str:

@@ -52,6 +52,7 @@ typedef struct {
     double c_floor;    /* sound-speed floor: p >= rho c_floor^2 / gamma */
     int riemann;       /* ORC_RIEMANN_EXACT or ORC_RIEMANN_TWO_SHOCK */
     int slope;         /* ORC_SLOPE_MINMOD, ORC_SLOPE_MC or ORC_SLOPE_NONE */
+    int trace;         /* ORC_TRACE_MUSCL_HANCOCK or ORC_TRACE_CHARACTERISTIC */
 } orc_params;
 
 /* Scheme variants (the HYDRO options the paper leaves to its ref. [5]):
@@ -62,6 +63,7 @@ typedef struct {
  * Godunov).  The defaults are the exact solver and minmod. */
 enum { ORC_RIEMANN_EXACT = 0, ORC_RIEMANN_TWO_SHOCK = 1 };
 enum { ORC_SLOPE_MINMOD = 0, ORC_SLOPE_MC = 1, ORC_SLOPE_NONE = 2 };
+enum { ORC_TRACE_MUSCL_HANCOCK = 0, ORC_TRACE_CHARACTERISTIC = 1 };
 
 enum { ORC_BC_REFLECT = 0, ORC_BC_TRANSMISSIVE = 1, ORC_BC_PERIODIC = 2 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENEGATIVE = 4 };
@@ -162,12 +164,20 @@ static double limited_slope(const orc_params *P, double a, double b)
  * rho: u D_rho + rho D_u;  u_n: u D_u + D_p / rho;  u_t: u D_ut;
  * p: gamma p D_u + u D_p).  Face states: WL = W - D/2 + dW at the cell's
  * left face, WR = W + D/2 + dW at its right face, each floored. */
+static void characteristic_trace(const orc_params *P, double dtdx,
+                                 const double W0[4], const double D[4],
+                                 double WL[4], double WR[4]);
+
 static void muscl_hancock_trace(const orc_params *P, double dtdx,
                                 const double Wm[4], const double W0[4],
                                 const double Wp[4], double WL[4], double WR[4])
 {
     double D[4], dW[4];
     for (int q = 0; q < 4; q++) D[q] = limited_slope(P, W0[q] - Wm[q], Wp[q] - W0[q]);
+    if (P->trace == ORC_TRACE_CHARACTERISTIC) {
+        characteristic_trace(P, dtdx, W0, D, WL, WR);
+        return;
+    }
 
     double rho = W0[0], u = W0[1], p = W0[3];
     double half = -0.5 * dtdx;
@@ -179,6 +189,53 @@ static void muscl_hancock_trace(const orc_params *P, double dtdx,
     for (int q = 0; q < 4; q++) {
         WL[q] = W0[q] - 0.5 * D[q] + dW[q];
         WR[q] = W0[q] + 0.5 * D[q] + dW[q];
+    }
+    WL[0] = floor_rho(P, WL[0]);
+    WR[0] = floor_rho(P, WR[0]);
+    WL[3] = floor_p(P, WL[0], WL[3]);
+    WR[3] = floor_p(P, WR[0], WR[3]);
+}
+
+/* Characteristic tracing (the trace variant).  The limited slopes D are
+ * split into the waves of the primitive Jacobian A(W) (speeds u - c, u, u,
+ * u + c): amplitudes
+ *   a1 = -rho/(2c) D_u + D_p/(2c^2),  a2 = D_rho - D_p/c^2,
+ *   a3 = D_ut,                        a4 =  rho/(2c) D_u + D_p/(2c^2),
+ * right eigenvectors r1 = (1, -c/rho, 0, c^2), r2 = (1, 0, 0, 0),
+ * r3 = (0, 0, 1, 0), r4 = (1, c/rho, 0, c^2).  The MUSCL-Hancock faces are
+ * W + 1/2 sum_k (1 - nu_k) a_k r_k (right) and W - 1/2 sum_k (1 + nu_k) a_k
+ * r_k (left), nu_k = lambda_k dt/dx, over every wave; here each face takes
+ * only the waves moving toward it: lambda_k > 0 for the right face,
+ * lambda_k < 0 for the left one (a wave at rest reaches neither).  Faces
+ * floored as in the MUSCL-Hancock trace. */
+static void characteristic_trace(const orc_params *P, double dtdx,
+                                 const double W0[4], const double D[4],
+                                 double WL[4], double WR[4])
+{
+    double rho = W0[0], u = W0[1], p = W0[3];
+    double c = sound_speed(P, W0);
+    double a[4], lam[4], r[4][4];
+    a[0] = -rho / (2.0 * c) * D[1] + D[3] / (2.0 * c * c);
+    a[1] = D[0] - D[3] / (c * c);
+    a[2] = D[2];
+    a[3] = rho / (2.0 * c) * D[1] + D[3] / (2.0 * c * c);
+    lam[0] = u - c; lam[1] = u; lam[2] = u; lam[3] = u + c;
+    double r1[4] = {1.0, -c / rho, 0.0, c * c}, r2[4] = {1.0, 0.0, 0.0, 0.0};
+    double r3[4] = {0.0, 0.0, 1.0, 0.0}, r4[4] = {1.0, c / rho, 0.0, c * c};
+    for (int q = 0; q < 4; q++) {
+        r[0][q] = r1[q]; r[1][q] = r2[q]; r[2][q] = r3[q]; r[3][q] = r4[q];
+    }
+    (void)p;
+    for (int q = 0; q < 4; q++) {
+        WL[q] = W0[q];
+        WR[q] = W0[q];
+    }
+    for (int k = 0; k < 4; k++) {
+        double nu = lam[k] * dtdx;
+        for (int q = 0; q < 4; q++) {
+            if (lam[k] > 0.0) WR[q] += 0.5 * (1.0 - nu) * a[k] * r[k][q];
+            if (lam[k] < 0.0) WL[q] -= 0.5 * (1.0 + nu) * a[k] * r[k][q];
+        }
     }
     WL[0] = floor_rho(P, WL[0]);
     WR[0] = floor_rho(P, WR[0]);

@@ -48,6 +48,7 @@ struct Consts {
     int g75;      // g = 7/5: z = 1/7, G4 = 5, G3 = 7 (a 7th root and integer powers)
     int two_shock;  // Riemann solver variant: the two-shock pressure function on both sides
     int slope;      // slope variant: SLOPE_MINMOD, SLOPE_MC or SLOPE_NONE
+    int char_trace; // trace variant: characteristic tracing instead of MUSCL-Hancock
                     // (both read only by code compiled with SV = true: the kernels
                     // are instantiated once for the defaults, with no test of these
                     // flags, and once for any variant)
@@ -338,6 +339,47 @@ __device__ __forceinline__ bool positive(float x) {
     return i > 0 && i <= 0x7f800000;
 }
 
+// Characteristic tracing (the trace variant) of the cell W0 with limited
+// slopes D: the slopes split into the waves of the primitive Jacobian
+// (speeds u - c, u, u, u + c; amplitudes a1 = -rho/(2c) D_u + D_p/(2c^2),
+// a2 = D_rho - D_p/c^2, a3 = D_ut, a4 = rho/(2c) D_u + D_p/(2c^2); right
+// eigenvectors (1, -c/rho, 0, c^2), (1, 0, 0, 0), (0, 0, 1, 0),
+// (1, c/rho, 0, c^2)); the right face takes (1 - nu_k)/2 a_k r_k of the
+// waves with speed > 0, the left face -(1 + nu_k)/2 a_k r_k of those with
+// speed < 0 (nu_k = speed dt/dx), in wave order; floored as the trace.
+template <class T>
+__device__ __forceinline__ void characteristic_trace(const Consts<T>& K, T hdtdx, const Prim<T>& W0, T ir0,
+                                                     T Dr, T Du, T Dv, T Dp, Prim<T>& WL, Prim<T>& WR) {
+    const T c = tsqrt(K.gamma * W0.p * ir0);
+    const T ic = trcp(c);
+    const T ic2 = ic * ic;
+    const T rc = W0.r * ic, cr = c * ir0, c2 = c * c;
+    const T hp = T(0.5) * Dp * ic2;
+    const T a1 = tfma(T(-0.5) * rc, Du, hp), a2 = tfma(-Dp, ic2, Dr), a4 = tfma(T(0.5) * rc, Du, hp);
+    const T dtdx = T(-2) * hdtdx;
+    WL = W0;
+    WR = W0;
+    auto wave = [&](T lam, T a, T rr, T ru, T rv, T rp) {
+        if (lam > T(0)) {
+            const T s = T(0.5) * tfma(-lam, dtdx, T(1)) * a;
+            WR.r = tfma(s, rr, WR.r); WR.u = tfma(s, ru, WR.u); WR.v = tfma(s, rv, WR.v); WR.p = tfma(s, rp, WR.p);
+        }
+        if (lam < T(0)) {
+            const T s = T(-0.5) * tfma(lam, dtdx, T(1)) * a;
+            WL.r = tfma(s, rr, WL.r); WL.u = tfma(s, ru, WL.u); WL.v = tfma(s, rv, WL.v); WL.p = tfma(s, rp, WL.p);
+        }
+    };
+    wave(W0.u - c, a1, T(1), -cr, T(0), c2);
+    wave(W0.u, a2, T(1), T(0), T(0), T(0));
+    wave(W0.u, Dv, T(0), T(0), T(1), T(0));
+    wave(W0.u + c, a4, T(1), cr, T(0), c2);
+    WL.r = below_floor(WL.r, K.rho_floor) ? K.rho_floor : WL.r;
+    WR.r = below_floor(WR.r, K.rho_floor) ? K.rho_floor : WR.r;
+    const T pml = WL.r * K.cf2g, pmr = WR.r * K.cf2g;
+    WL.p = below_floor(WL.p, pml) ? pml : WL.p;
+    WR.p = below_floor(WR.p, pmr) ? pmr : WR.p;
+}
+
 // MUSCL-Hancock trace of the cell with primitive state W0 between Wm and Wp
 // (§1, second order): slopes D = minmod of one-sided differences; half-step
 // predictor dW = -(dt/dx)/2 A(W0) D with the primitive Jacobian rows
@@ -368,6 +410,10 @@ __device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) *
         Du = limited_slope(K, W0.u - Wm.u, Wp.u - W0.u);
         Dv = limited_slope(K, W0.v - Wm.v, Wp.v - W0.v);
         Dp = limited_slope(K, W0.p - Wm.p, Wp.p - W0.p);
+    }
+    if (SV && K.char_trace) {
+        characteristic_trace(K, hdtdx, W0, ir0, Dr, Du, Dv, Dp, WL, WR);
+        return;
     }
     const T dr = hdtdx * tfma(W0.u, Dr, W0.r * Du);
     const T du = hdtdx * tfma(W0.u, Du, Dp * ir0);

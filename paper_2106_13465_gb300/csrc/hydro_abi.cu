@@ -55,6 +55,7 @@ Consts<T> make_consts(const hydro_params& p, double tol) {
     K.g75 = (g == 1.4) ? 1 : 0;
     K.two_shock = p.riemann_solver == HYDRO_RIEMANN_TWO_SHOCK ? 1 : 0;
     K.slope = p.slope_type == HYDRO_SLOPE_MC ? SLOPE_MC : (p.slope_type == HYDRO_SLOPE_NONE ? SLOPE_NONE : SLOPE_MINMOD);
+    K.char_trace = p.trace_type == HYDRO_TRACE_CHARACTERISTIC ? 1 : 0;
     double c = 1.0, z = (g - 1.0) / (2.0 * g);
     for (int k = 1; k <= kBinomTerms; ++k) {
         c *= (z - (k - 1)) / k;  // C(z, k)
@@ -168,6 +169,8 @@ hydro_status validate_params(const hydro_params* p) {
         return fail(nullptr, HYDRO_EINVAL, "riemann_solver must be HYDRO_RIEMANN_EXACT or HYDRO_RIEMANN_TWO_SHOCK");
     if (p->slope_type < HYDRO_SLOPE_MINMOD || p->slope_type > HYDRO_SLOPE_NONE)
         return fail(nullptr, HYDRO_EINVAL, "slope_type must be HYDRO_SLOPE_MINMOD, _MC or _NONE");
+    if (p->trace_type != HYDRO_TRACE_MUSCL_HANCOCK && p->trace_type != HYDRO_TRACE_CHARACTERISTIC)
+        return fail(nullptr, HYDRO_EINVAL, "trace_type must be HYDRO_TRACE_MUSCL_HANCOCK or _CHARACTERISTIC");
     if (p->ngrids < 1 || !p->grids)
         return fail(nullptr, HYDRO_EINVAL, "need ngrids >= 1 and a grids array");
     for (int g = 0; g < p->ngrids; ++g) {

@@ -1002,7 +1002,7 @@ constexpr int launch_smem_bytes() {
 // SV = true read the variant flags; the others have the defaults built in).
 template <class T>
 bool scheme_variant(const Consts<T>& K) {
-    return K.two_shock || K.slope != SLOPE_MINMOD;
+    return K.two_shock || K.slope != SLOPE_MINMOD || K.char_trace;
 }
 
 // Launch (the dynamic shared-memory limit was raised by occupancy_one, which

@@ -23,6 +23,7 @@ BC_REFLECT, BC_TRANSMISSIVE, BC_PERIODIC = 0, 1, 2
 PREC_FP32, PREC_FP64 = 32, 64
 RIEMANN_EXACT, RIEMANN_TWO_SHOCK = 0, 1
 SLOPE_MINMOD, SLOPE_MC, SLOPE_NONE = 0, 1, 2
+TRACE_MUSCL_HANCOCK, TRACE_CHARACTERISTIC = 0, 1
 STATUS_NAMES = {0: "HYDRO_OK", 1: "HYDRO_EINVAL", 2: "HYDRO_ENOMEM", 3: "HYDRO_ECUDA",
                 4: "HYDRO_ENEGATIVE", 5: "HYDRO_ETIMEOUT"}
 
@@ -44,7 +45,8 @@ class hydro_params(ctypes.Structure):
                 ("niter_riemann", ctypes.c_int), ("rho_floor", ctypes.c_double),
                 ("c_floor", ctypes.c_double), ("ngrids", ctypes.c_int),
                 ("grids", ctypes.POINTER(hydro_grid)), ("cuda_stream", ctypes.c_void_p),
-                ("riemann_solver", ctypes.c_int), ("slope_type", ctypes.c_int)]
+                ("riemann_solver", ctypes.c_int), ("slope_type", ctypes.c_int),
+                ("trace_type", ctypes.c_int)]
 
 
 class hydro_tuning(ctypes.Structure):
@@ -224,9 +226,10 @@ def hydro_version() -> str:
 # ---- convenience wrapper -----------------------------------------------------
 def make_params(grids, precision: int = PREC_FP64, gamma: float = 1.4, cfl: float = 0.8,
                 niter: int = 10, rho_floor: float = 1e-10, c_floor: float = 1e-10,
-                stream: int | None = None, riemann: int = RIEMANN_EXACT, slope: int = SLOPE_MINMOD):
+                stream: int | None = None, riemann: int = RIEMANN_EXACT, slope: int = SLOPE_MINMOD,
+                trace: int = TRACE_MUSCL_HANCOCK):
     """grids: iterable of (nx, ny, h, (bc_xlo, bc_xhi, bc_ylo, bc_yhi));
-    riemann / slope select the scheme variants (include/hydro.h)."""
+    riemann / slope / trace select the scheme variants (include/hydro.h)."""
     grids = list(grids)
     arr = (hydro_grid * len(grids))()
     for k, (nx, ny, h, bc) in enumerate(grids):
@@ -234,7 +237,7 @@ def make_params(grids, precision: int = PREC_FP64, gamma: float = 1.4, cfl: floa
         for q in range(4):
             arr[k].bc[q] = int(bc[q])
     p = hydro_params(precision, gamma, cfl, niter, rho_floor, c_floor, len(grids),
-                     ctypes.cast(arr, ctypes.POINTER(hydro_grid)), stream or None, riemann, slope)
+                     ctypes.cast(arr, ctypes.POINTER(hydro_grid)), stream or None, riemann, slope, trace)
     return p, arr
 
 

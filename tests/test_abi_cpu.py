@@ -81,7 +81,8 @@ def test_no_gpu_reports_cuda_error_not_a_fallback():
     assert not ctx.value
 
 
-@pytest.mark.parametrize("kw,msg", [(dict(riemann=2), "riemann_solver"), (dict(slope=3), "slope_type")])
+@pytest.mark.parametrize("kw,msg", [(dict(riemann=2), "riemann_solver"), (dict(slope=3), "slope_type"),
+                                    (dict(trace=5), "trace_type")])
 def test_invalid_scheme_variants_rejected(kw, msg):
     p, _arr = _params(**kw)
     st, ctx = H.hydro_init(p)

@@ -59,6 +59,12 @@ MUTANTS = {
                            "    m = fabs(2.0 * a);\n"),
     "mc_sign_lost": ("    return (a > 0.0) ? m : -m;", "    return m;"),
     "no_slope_is_minmod": ("    if (P->slope == ORC_SLOPE_NONE) return 0.0;\n", ""),
+    "char_eigvec_sign": ("double r1[4] = {1.0, -c / rho, 0.0, c * c}", "double r1[4] = {1.0, c / rho, 0.0, c * c}"),
+    "char_amplitude_half": ("a[3] = rho / (2.0 * c) * D[1] + D[3] / (2.0 * c * c);",
+                            "a[3] = rho / (2.0 * c) * D[1] + D[3] / (c * c);"),
+    "char_nu_sign": ("if (lam[k] > 0.0) WR[q] += 0.5 * (1.0 - nu) * a[k] * r[k][q];",
+                     "if (lam[k] > 0.0) WR[q] += 0.5 * (1.0 + nu) * a[k] * r[k][q];"),
+    "char_all_waves_right": ("if (lam[k] > 0.0) WR[q]", "if (1) WR[q]"),
 }
 
 

@@ -134,3 +134,95 @@ def test_first_order_scheme_converges_at_first_order_on_smooth_flow():
             errs.append(np.abs(c - 0.5 * (f[0::2] + f[1::2])).mean())
         ratios = [errs[i] / errs[i + 1] for i in range(2)]
         assert all(lo < r < hi for r in ratios), (slope, ratios)
+
+
+# ---- characteristic tracing ----------------------------------------------
+CH = O.params(trace=O.TRACE_CHARACTERISTIC)
+
+
+def _c_of(w):
+    return math.sqrt(G * w[3] / w[0])
+
+
+@pytest.mark.parametrize("sgn", [1.0, -1.0])
+def test_characteristic_trace_supersonic_keeps_all_waves_on_one_face(sgn):
+    """Flow faster than sound: every wave moves the same way, so the downwind
+    face is the full MUSCL-Hancock face and the upwind face is the cell
+    state itself (the wave split of the slopes recombines them)."""
+    c = _c_of([1.0, 0.0, 0.0, 1.0])
+    u = sgn * 2.5 * c
+    wm, w0, wp = [0.9, u - 0.02, 0.1, 0.95], [1.0, u, 0.12, 1.0], [1.08, u + 0.03, 0.15, 1.07]
+    wl, wr = O.trace(0.2, wm, w0, wp, CH)
+    ml, mr = O.trace(0.2, wm, w0, wp)
+    if sgn > 0:
+        np.testing.assert_array_equal(wl, w0)
+        np.testing.assert_allclose(wr, mr, rtol=1e-13, atol=1e-15)
+    else:
+        np.testing.assert_array_equal(wr, w0)
+        np.testing.assert_allclose(wl, ml, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("wave", [1, 4])
+def test_characteristic_trace_of_a_simple_acoustic_slope(wave):
+    """Subsonic flow (0 < u < c) with the slope along one acoustic
+    eigenvector r = (1, -+c/rho, 0, c^2) of amplitude e: the u + c wave reaches
+    only the right face, W + (1 - (u + c) dt/dx)/2 e r4; the u - c wave only
+    the left one, W - (1 + (u - c) dt/dx)/2 e r1."""
+    rho, u, p = 1.0, 0.3, 1.0
+    c = math.sqrt(G * p / rho)
+    e, dtdx = 1e-3, 0.25
+    s = 1.0 if wave == 4 else -1.0
+    r = np.array([1.0, s * c / rho, 0.0, c * c])
+    w0 = np.array([rho, u, 0.0, p])
+    wl, wr = O.trace(dtdx, w0 - e * r, w0, w0 + e * r, CH)
+    lam = u + s * c
+    if wave == 4:
+        np.testing.assert_allclose(wr, w0 + 0.5 * (1 - lam * dtdx) * e * r, rtol=1e-13)
+        np.testing.assert_allclose(wl, w0, rtol=1e-13)
+    else:
+        np.testing.assert_allclose(wl, w0 - 0.5 * (1 + lam * dtdx) * e * r, rtol=1e-13)
+        np.testing.assert_allclose(wr, w0, rtol=1e-13)
+
+
+def test_characteristic_trace_contact_reduces_to_the_scalar_scheme():
+    """A contact carried at u > 0 through uniform pressure: only the entropy
+    wave moves, toward the right face, so the scheme is the textbook scalar
+    minmod MUSCL-Hancock scheme again."""
+    n, a, p0 = 64, 0.6, 1.0
+    x = (np.arange(n) + 0.5) / n
+    rho = 1.0 + 0.3 * np.sin(2 * np.pi * x) + 0.2 * (np.abs(x - 0.3) < 0.1)
+    U = pr.conserved(np.tile(rho, (2, 1)), a, 0.0, p0)
+    h = 1.0 / n
+    dt = 0.8 * h / (a + math.sqrt(G * p0 / rho.min()))
+    nu = a * dt / h
+    out, _, _ = O.run(U, h, (pr.PERIODIC,) * 4, 20, dt_override=[dt] * 20, P=CH)
+
+    q = rho.copy()
+    for _ in range(20):
+        dm = q - np.roll(q, 1)
+        dp = np.roll(q, -1) - q
+        s = np.where(dm * dp > 0, np.where(np.abs(dm) < np.abs(dp), dm, dp), 0.0)
+        face = q + 0.5 * (1.0 - nu) * s
+        q = q - nu * (face - np.roll(face, 1))
+    assert np.allclose(out[0, 0], q, rtol=2e-14, atol=0)
+
+
+def test_characteristic_trace_sod_converges():
+    """The Sod problem with characteristic tracing approaches the exact
+    profile as the grid is refined (L1 error of density falls)."""
+    wl, wr = [1.0, 0.0, 0.0, 1.0], [0.125, 0.0, 0.0, 0.1]
+    errs = []
+    for n in (64, 128, 256):
+        pb = pr.sod(n, 2, 0)
+        t, k, U = 0.0, 0, pb.U.copy()
+        while t < 0.2 * (1 - 1e-14):
+            dt = min(O.cfl_dt(U, pb.h, CH), 0.2 - t)
+            U, _, _ = O.run(U, pb.h, pb.bc, 1, step0=k, dt_override=[dt], P=CH)
+            t += dt
+            k += 1
+        x = (np.arange(n) + 0.5) / n - 0.5
+        ps, us = O.riemann_star(wl, wr)
+        exact = np.array([O.sample(wl, wr, ps, us, xi / 0.2)[0] for xi in x])
+        errs.append(np.abs(U[0, 0] - exact).mean())
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.012

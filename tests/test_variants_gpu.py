@@ -1,6 +1,6 @@
-"""Scheme variants on the GPU (hydro_params.riemann_solver, slope_type):
-the two-shock approximate Riemann solver and the monotonized central and
-first-order slopes, each against the oracle run with the same variant, in
+"""Scheme variants on the GPU (hydro_params.riemann_solver, slope_type,
+trace_type): the two-shock approximate Riemann solver, the monotonized
+central and first-order slopes and characteristic tracing, each against the oracle run with the same variant, in
 FP64 to the parity tolerance, and FP32 to a stated density error; the fused
 step kernel gives the split sweeps' bits with a variant too."""
 import numpy as np
@@ -15,10 +15,12 @@ pytestmark = pytest.mark.gpu
 T_ = pr.TRANSMISSIVE
 TOL64 = 1e-11
 VARIANTS = [
-    ("two_shock", H.RIEMANN_TWO_SHOCK, H.SLOPE_MINMOD),
-    ("mc", H.RIEMANN_EXACT, H.SLOPE_MC),
-    ("first_order", H.RIEMANN_EXACT, H.SLOPE_NONE),
-    ("two_shock_mc", H.RIEMANN_TWO_SHOCK, H.SLOPE_MC),
+    ("two_shock", H.RIEMANN_TWO_SHOCK, H.SLOPE_MINMOD, H.TRACE_MUSCL_HANCOCK),
+    ("mc", H.RIEMANN_EXACT, H.SLOPE_MC, H.TRACE_MUSCL_HANCOCK),
+    ("first_order", H.RIEMANN_EXACT, H.SLOPE_NONE, H.TRACE_MUSCL_HANCOCK),
+    ("two_shock_mc", H.RIEMANN_TWO_SHOCK, H.SLOPE_MC, H.TRACE_MUSCL_HANCOCK),
+    ("characteristic", H.RIEMANN_EXACT, H.SLOPE_MINMOD, H.TRACE_CHARACTERISTIC),
+    ("characteristic_mc", H.RIEMANN_EXACT, H.SLOPE_MC, H.TRACE_CHARACTERISTIC),
 ]
 
 
@@ -44,12 +46,13 @@ CASES = [lambda: pr.sedov(96, 80), lambda: pr.random_modes(128, 90, seed=7), lam
          lambda: _vacuum_pair()]
 
 
-@pytest.mark.parametrize("name,riemann,slope", VARIANTS, ids=[v[0] for v in VARIANTS])
-def test_variant_fp64_matches_oracle(name, riemann, slope):
+@pytest.mark.parametrize("name,riemann,slope,trace", VARIANTS, ids=[v[0] for v in VARIANTS])
+def test_variant_fp64_matches_oracle(name, riemann, slope, trace):
     for make in CASES:
         pb = make()
-        want, odts, _ = O.run(pb.U, pb.h, pb.bc, 10, P=O.params(riemann=riemann, slope=slope))
-        with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=64, riemann=riemann, slope=slope) as c:
+        want, odts, _ = O.run(pb.U, pb.h, pb.bc, 10, P=O.params(riemann=riemann, slope=slope, trace=trace))
+        with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=64, riemann=riemann, slope=slope,
+                       trace=trace) as c:
             c.set_state(0, pb.U)
             dts = c.step(10, record_dt=True)
             got = c.get_state(0)
@@ -60,13 +63,14 @@ def test_variant_fp64_matches_oracle(name, riemann, slope):
         assert not np.array_equal(base, want), (name, pb.name)
 
 
-@pytest.mark.parametrize("name,riemann,slope", VARIANTS, ids=[v[0] for v in VARIANTS])
-def test_variant_fp32_density_error_and_fused(name, riemann, slope):
+@pytest.mark.parametrize("name,riemann,slope,trace", VARIANTS, ids=[v[0] for v in VARIANTS])
+def test_variant_fp32_density_error_and_fused(name, riemann, slope, trace):
     pb = pr.random_modes(128, 90, seed=7)
-    ref, dts, _ = O.run(pb.U, pb.h, pb.bc, 10, P=O.params(riemann=riemann, slope=slope))
+    ref, dts, _ = O.run(pb.U, pb.h, pb.bc, 10, P=O.params(riemann=riemann, slope=slope, trace=trace))
     outs = {}
     for fused in (0, 1):
-        with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=32, riemann=riemann, slope=slope) as c:
+        with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=32, riemann=riemann, slope=slope,
+                       trace=trace) as c:
             c.set_tuning(fused=fused, graph_steps=0)
             c.set_state(0, pb.U)
             c.step(10, dt_override=dts)
@@ -80,4 +84,6 @@ def test_variant_arguments_checked():
     p, _arr = H.make_params([(16, 16, 1 / 16, (0, 0, 0, 0))], riemann=2)
     assert H.hydro_init(p)[0] == H.HYDRO_EINVAL
     p, _arr = H.make_params([(16, 16, 1 / 16, (0, 0, 0, 0))], slope=3)
+    assert H.hydro_init(p)[0] == H.HYDRO_EINVAL
+    p, _arr = H.make_params([(16, 16, 1 / 16, (0, 0, 0, 0))], trace=2)
     assert H.hydro_init(p)[0] == H.HYDRO_EINVAL
