@@ -116,9 +116,10 @@ typedef struct {
  *   ctas_per_sm   resident CTAs per SM of the persistent sweep launches
  *                 (at most the occupancy limit)
  *   graph_steps   steps captured per CUDA graph (even, 0 = no graph)
- *   span_len      x sweep: results of a row per warp task (a multiple of 60:
- *                 a warp walks a row in overlapping 64-cell segments that
- *                 yield 60 results each)
+ *   span_len      x sweep: results of a row per warp task (a multiple of 60).
+ *                 FP32: a warp walks a row in overlapping 64-cell segments
+ *                 that yield 60 results each.  FP64: a warp walks 32 rows
+ *                 at once, a lane per row, over span_len cells.
  *   fused         0: a step is two sweep launches, one per direction (the
  *                 state crosses HBM once per sweep).  1: a step is one
  *                 launch of the fused step kernel, which sweeps both

@@ -179,9 +179,9 @@ __device__ __forceinline__ void fused_y_col(const SweepArgs<T>& a, T* box, int c
     if (!active) return;
     YWalk<T> w = {};
     w.u0 = lead0;
-    w.w0 = cons_to_prim(K, lead0);
     w.u1 = lead1;
     w.w1 = cons_to_prim(K, lead1, w.ir1);
+    w.dl = pdiff(w.w1, cons_to_prim(K, lead0));
     T* __restrict__ q0 = a.dst + g.off + x;
     unsigned wk = 0;
 #pragma unroll 1
@@ -190,7 +190,8 @@ __device__ __forceinline__ void fused_y_col(const SweepArgs<T>& a, T* box, int c
         T ir2;
         const Prim<T> w2 = cons_to_prim(K, u, ir2);
         Prim<T> wl1, wr1;
-        trace<T, SV>(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
+        const Prim<T> dr = pdiff(w2, w.w1);
+        trace<T, SV>(K, hdtdx, w.w1, w.ir1, w.dl, dr, wl1, wr1);  // cell k - 1
         if (k == s0) w.wr0 = wl1;  // the face left of cell s0-1 is not formed: a throw-away problem
         bool rd = false;
         const Cons<T> fhi = FluxOp<T, VAR, SV>::eval(a, w.wr0, wl1, rd, nfb, wk);  // (k-1) - 1/2
@@ -211,7 +212,7 @@ __device__ __forceinline__ void fused_y_col(const SweepArgs<T>& a, T* box, int c
         }
         w.flo = fhi;
         w.u0 = w.u1;
-        w.w0 = w.w1;
+        w.dl = dr;
         w.wr0 = wr1;
         w.u1 = u;
         w.w1 = w2;

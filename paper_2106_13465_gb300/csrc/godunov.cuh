@@ -28,7 +28,7 @@ template <class T>
 struct Consts {
     T gamma;      // ratio of specific heats g
     T gm1;        // g - 1
-    T inv_gm1;    // 1 / (g - 1)
+    T g_gm1;      // g / (g - 1)
     T z;          // (g - 1) / (2 g): rarefaction exponent
     T zs;         // (g + 1) / (2 g): shock-speed factor
     T G3;         // 2 g / (g - 1)
@@ -39,7 +39,6 @@ struct Consts {
     T inv_g;      // 1 / g
     T hgp1;       // (g + 1) / 2
     T sqg;        // sqrt(g)
-    T isqg;       // 1 / sqrt(g)
     T rho_floor;  // density floor
     T cf2g;       // c_floor^2 / g: p >= rho * cf2g
     T pmin;       // smallest pressure of the Riemann iteration, rho_floor * cf2g
@@ -112,6 +111,13 @@ __device__ __forceinline__ bool gt_pos(double a, double b) {
     return __double_as_longlong(a) > __double_as_longlong(b);
 }
 __device__ __forceinline__ bool gt_pos(float a, float b) { return a > b; }
+// |x| > b for b >= +0 not NaN, on the magnitude's bit pattern (a NaN x
+// counts as greater)
+__device__ __forceinline__ bool abs_gt_pos(double x, double b) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) >
+           (unsigned long long)__double_as_longlong(b);
+}
+__device__ __forceinline__ bool abs_gt_pos(float x, float b) { return !(fabsf(x) <= b); }
 __device__ __forceinline__ bool eq_pos(double a, double b) {
     return __double_as_longlong(a) == __double_as_longlong(b);
 }
@@ -146,11 +152,14 @@ __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a
 // x^(1/7) for a positive normal double, within 3 ulp (a 7th root by Newton's
 // method for nth roots, taken to third order):  write x = m 2^(7q) with m in
 // [1, 2^7); v0 ~ m^(-1/7) from the FP32 hardware log2 and exp2 (relative
-// error below 1e-6); h = m v0^7 - 1 with one rounding (fused multiply-add);
-// then m^(1/7) = m v0^6 (1 + h)^(-6/7), the binomial series to h^3 (the
-// remainder is below 1e-22) -- ten FP64 operations, no division.  A rounding
-// error d in v0^6 moves the result by only d/7, since it enters h as well.
-// The exponent q is added to the result's exponent field.  Other x: exp2/log2.
+// error below 1e-6), improved by one FP32 Newton step v0 (1 + (1 - m v0^7)/7)
+// (relative error below 1e-7: the FP32 roundings and m's 24-bit FP32 copy);
+// h = m v0^7 - 1 with one rounding (fused multiply-add), |h| < 1e-6; then
+// m^(1/7) = m v0^6 (1 + h)^(-6/7), the binomial series to h^2 (the
+// remainder is below 1e-18 of an ulp's 1.1e-16) -- nine FP64 operations, no
+// division.  A rounding error d in v0^6 moves the result by only d/7, since
+// it enters h as well.  The exponent q is added to the result's exponent
+// field.  Other x: exp2/log2.
 __device__ __forceinline__ double root7(double x) {
     const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
     const int ex = (int)((hi >> 20) & 0x7ffu);
@@ -165,13 +174,17 @@ __device__ __forceinline__ double root7(double x) {
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(mf));
     t = t * (-1.0f / 7.0f);
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(t));
-    // t in (1/2, 1]: exact conversion to double on the integer pipe
+    {  // one FP32 Newton step (t stays in [1/2, 1])
+        const float t2 = t * t, t4 = t2 * t2, t7 = t4 * t2 * t;
+        t = fmaf(t * (1.0f / 7.0f), fmaf(-mf, t7, 1.0f), t);
+    }
+    // t in [1/2, 1]: exact conversion to double on the integer pipe
     const unsigned fb = __float_as_uint(t);
     const double v0 = __hiloint2double((int)((((fb >> 23) + (1023u - 127u)) << 20) | ((fb & 0x7fffffu) >> 3)),
                                        (int)(fb << 29));
     const double v2 = v0 * v0, v3 = v2 * v0, v6 = v3 * v3, v7 = v6 * v0;
     const double h = fma(m, v7, -1.0);
-    const double P = fma(fma(h, -260.0 / 343.0, 39.0 / 49.0), h, -6.0 / 7.0);  // (1+h)^(-6/7) = 1 + h P
+    const double P = fma(h, 39.0 / 49.0, -6.0 / 7.0);  // (1+h)^(-6/7) = 1 + h P + O(h^3)
     const double base = m * v6;
     const double y = fma(base, h * P, base);
     return __hiloint2double((int)((unsigned)__double2hiint(y) + ((unsigned)q << 20)), __double2loint(y));
@@ -210,8 +223,8 @@ __device__ __forceinline__ Prim<T> cons_to_prim(const Consts<T>& K, const Cons<T
     ir = trcp(W.r);
     W.u = U.mn * ir;
     W.v = U.mt * ir;
-    const T q2 = tfma(W.u, W.u, W.v * W.v);
-    T p = K.gm1 * tfma(T(-0.5) * W.r, q2, U.E);
+    // p = (g-1) E - (g-1)/2 rho |u|^2, with rho |u|^2 = m_n u_n + m_t u_t
+    T p = tfma(-K.G7, tfma(U.mn, W.u, U.mt * W.v), K.gm1 * U.E);
     const T pm = W.r * K.cf2g;
     W.p = below_floor(p, pm) ? pm : p;
     return W;
@@ -287,8 +300,9 @@ __device__ __forceinline__ T limited_slope(const Consts<T>& K, T a, T b) {
     return T(0);
 }
 
-// Exact shortcuts for states equal bit for bit, per arithmetic type: the
-// trace between equal neighbours (trace), the Riemann problem of equal states
+// Exact shortcuts for equal states, per arithmetic type: the trace of a cell
+// whose one-sided differences vanish (trace), the Riemann problem of states
+// equal bit for bit
 // (equal_state_flux) and, in the sweeps, uniform 5-point stencils (a cell
 // whose stencil is uniform is copied).  Each saves arithmetic where the state
 // is uniform and costs a few integer instructions per cell elsewhere.  FP64
@@ -380,48 +394,73 @@ __device__ __forceinline__ void characteristic_trace(const Consts<T>& K, T hdtdx
     WR.p = below_floor(WR.p, pmr) ? pmr : WR.p;
 }
 
-// MUSCL-Hancock trace of the cell with primitive state W0 between Wm and Wp
-// (§1, second order): slopes D = minmod of one-sided differences; half-step
-// predictor dW = -(dt/dx)/2 A(W0) D with the primitive Jacobian rows
+// Differences of primitive states, a - b.
+template <class T>
+__device__ __forceinline__ Prim<T> pdiff(const Prim<T>& a, const Prim<T>& b) {
+    return Prim<T>{a.r - b.r, a.u - b.u, a.v - b.v, a.p - b.p};
+}
+
+// Whether every component of both differences is +-0 (bit patterns).
+__device__ __forceinline__ bool zero_diffs(const Prim<double>& a, const Prim<double>& b) {
+    const unsigned long long o =
+        (unsigned long long)(__double_as_longlong(a.r) | __double_as_longlong(a.u) | __double_as_longlong(a.v) |
+                             __double_as_longlong(a.p) | __double_as_longlong(b.r) | __double_as_longlong(b.u) |
+                             __double_as_longlong(b.v) | __double_as_longlong(b.p));
+    return (o << 1) == 0ull;
+}
+__device__ __forceinline__ bool zero_diffs(const Prim<float>& a, const Prim<float>& b) {
+    const unsigned o = (unsigned)(__float_as_int(a.r) | __float_as_int(a.u) | __float_as_int(a.v) |
+                                  __float_as_int(a.p) | __float_as_int(b.r) | __float_as_int(b.u) |
+                                  __float_as_int(b.v) | __float_as_int(b.p));
+    return (o << 1) == 0u;
+}
+
+// MUSCL-Hancock trace of the cell with primitive state W0 (§1, second
+// order), given the one-sided differences dl = W0 - W_(i-1) and
+// dr = W_(i+1) - W0 (a line walk passes a cell's dr on as the next cell's
+// dl): slopes D = minmod(dl, dr); half-step predictor
+// dW = -(dt/dx)/2 A(W0) D with the primitive Jacobian rows
 //   rho: u D_rho + rho D_u,  u_n: u D_u + D_p/rho,  u_t: u D_ut,
 //   p: g p D_u + u D_p;
 // faces WL = W0 - D/2 + dW (left), WR = W0 + D/2 + dW (right), floored.
 //
-// Between two neighbours equal to it (bit for bit) every slope is 0, the
-// predictor is -0 and each face equals W0 exactly (W0 is already floored):
-// that case returns W0 without the arithmetic.
+// Where every difference is zero every slope is 0 and each face is W0 (to
+// the sign of a zero component; W0 is already floored): that case returns
+// W0 without the arithmetic.
 template <class T, bool SV = false>
-__device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) */,
-                                      const Prim<T>& Wm, const Prim<T>& W0, T ir0 /* 1/rho_0 */,
-                                      const Prim<T>& Wp, Prim<T>& WL, Prim<T>& WR) {
-    if (Shortcuts<T>::trace && (diff_bits(Wm, W0) | diff_bits(Wp, W0)) == 0) {
+__device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) */, const Prim<T>& W0,
+                                      T ir0 /* 1/rho_0 */, const Prim<T>& dl, const Prim<T>& dr,
+                                      Prim<T>& WL, Prim<T>& WR) {
+    if (Shortcuts<T>::trace && zero_diffs(dl, dr)) {
         WL = W0;
         WR = W0;
         return;
     }
     T Dr, Du, Dv, Dp;
     if (!SV || K.slope == SLOPE_MINMOD) {
-        Dr = minmod(W0.r - Wm.r, Wp.r - W0.r);
-        Du = minmod(W0.u - Wm.u, Wp.u - W0.u);
-        Dv = minmod(W0.v - Wm.v, Wp.v - W0.v);
-        Dp = minmod(W0.p - Wm.p, Wp.p - W0.p);
+        Dr = minmod(dl.r, dr.r);
+        Du = minmod(dl.u, dr.u);
+        Dv = minmod(dl.v, dr.v);
+        Dp = minmod(dl.p, dr.p);
     } else {
-        Dr = limited_slope(K, W0.r - Wm.r, Wp.r - W0.r);
-        Du = limited_slope(K, W0.u - Wm.u, Wp.u - W0.u);
-        Dv = limited_slope(K, W0.v - Wm.v, Wp.v - W0.v);
-        Dp = limited_slope(K, W0.p - Wm.p, Wp.p - W0.p);
+        Dr = limited_slope(K, dl.r, dr.r);
+        Du = limited_slope(K, dl.u, dr.u);
+        Dv = limited_slope(K, dl.v, dr.v);
+        Dp = limited_slope(K, dl.p, dr.p);
     }
     if (SV && K.char_trace) {
         characteristic_trace(K, hdtdx, W0, ir0, Dr, Du, Dv, Dp, WL, WR);
         return;
     }
-    const T dr = hdtdx * tfma(W0.u, Dr, W0.r * Du);
-    const T du = hdtdx * tfma(W0.u, Du, Dp * ir0);
-    const T dv = hdtdx * (W0.u * Dv);
-    const T dp = hdtdx * tfma(K.gamma * W0.p, Du, W0.u * Dp);
-    // faces (W0 + dW) -+ D/2: the predicted centre first, then one fused
-    // multiply-add per face (12 operations where W0 -+ D/2 + dW takes 16)
-    const T cr = W0.r + dr, cu = W0.u + du, cv = W0.v + dv, cp = W0.p + dp;
+    // the predicted centre W0 + dW, each row of dW a chain of fused
+    // multiply-adds on the scaled coefficients hu = -(dt/dx)/2 u and
+    // -(dt/dx)/2 rho, 1/rho, g p (11 operations), then one fused
+    // multiply-add per face (W0 + dW) -+ D/2
+    const T hu = hdtdx * W0.u;
+    const T cr = tfma(hu, Dr, tfma(hdtdx * W0.r, Du, W0.r));
+    const T cu = tfma(hu, Du, tfma(hdtdx * ir0, Dp, W0.u));
+    const T cv = tfma(hu, Dv, W0.v);
+    const T cp = tfma(hu, Dp, tfma((hdtdx * K.gamma) * W0.p, Du, W0.p));
     WL.r = tfma(T(-0.5), Dr, cr);
     WL.u = tfma(T(-0.5), Du, cu);
     WL.v = tfma(T(-0.5), Dv, cv);
@@ -454,10 +493,6 @@ struct Side {
     T r, u, v, p;  // traced state
     T c;           // sound speed
     T ip;          // 1 / p_K
-    T irc;         // 1 / (rho_K c_K)
-    T iA;          // 1 / A_K = (g+1)/2 rho_K
-    T B;           // B_K
-    T cG4;         // 2 c_K / (g-1)
 };
 
 template <class T>
@@ -465,22 +500,17 @@ __device__ __forceinline__ Side<T> make_side(const Consts<T>& K, const Prim<T>& 
     Side<T> s;
     s.r = W.r; s.u = W.u; s.v = W.v; s.p = W.p;
     if (sizeof(T) == 8) {
-        // y = 1/sqrt(rho p) gives c = sqrt(g) p y, 1/p = rho y^2 and
-        // 1/(rho c) = y / sqrt(g): one reciprocal square root per side
+        // y = 1/sqrt(rho p) gives c = sqrt(g) p y and 1/p = rho y^2: one
+        // reciprocal square root per side
         const T y = trsqrt(W.r * W.p);
         s.c = K.sqg * W.p * y;
         s.ip = W.r * y * y;
-        s.irc = K.isqg * y;
     } else {
         // FP32: rho p can underflow at the floors, so two reciprocals
         const T ir = T(1) / W.r;
         s.ip = T(1) / W.p;
         s.c = tsqrt(K.gamma * W.p * ir);
-        s.irc = s.c * s.ip * K.inv_g;
     }
-    s.iA = K.hgp1 * W.r;
-    s.B = K.G6 * W.p;
-    s.cG4 = s.c * K.G4;
     return s;
 }
 
@@ -492,16 +522,19 @@ template <class T, bool SV = false>
 __device__ __forceinline__ void pressure_fn(const Consts<T>& K, const Side<T>& s, T p,
                                             T& f, T& a, T& b, T& pz) {
     if (gt_pos(p, s.p) || (SV && K.two_shock)) {
-        const T q = trsqrt((p + s.B) * s.iA);
+        const T iA = K.hgp1 * s.r;                        // 1 / A_K
+        const T q = trsqrt(tfma(K.G6, s.p, p) * iA);      // p + B_K = p + G6 p_K
         const T dpk = p - s.p;
         f = dpk * q;
         a = T(0);
-        b = q * tfma(T(-0.5) * dpk, q * q * s.iA, T(1));
+        b = q * tfma(T(-0.5) * dpk, q * q * iA, T(1));
         pz = T(-1);
     } else {
+        // f_K = 2 c_K/(g-1) (pz - 1); a_K = pz p_K/(rho_K c_K) = pz c_K / g
         pz = pow_z(K, p, s.p, s.ip);
-        f = tfma(s.cG4, pz, -s.cG4);
-        a = pz * s.irc * s.p;
+        const T cG4 = s.c * K.G4;
+        f = tfma(cG4, pz, -cG4);
+        a = pz * (s.c * K.inv_g);
         b = T(0);
     }
 }
@@ -546,12 +579,14 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
         T pn = p - d;
         T rel = g;                                      // d / p
         if (below_floor(pn, K.pmin)) { pn = K.pmin; floored = true; d = p - pn; rel = tdiv(d, p); }
-        if (!gt_pos(tabs(d), K.tol * pn)) {
+        if (!abs_gt_pos(rel, K.tol)) {
             if (!is_zero(d)) {
-                fl -= tfma(al, rel, bl * d);
-                fr -= tfma(ar, rel, br * d);
-                if (positive(pzl)) pzl = tfma(-K.z * pzl, rel, pzl);
-                if (positive(pzr)) pzr = tfma(-K.z * pzr, rel, pzr);
+                // f_K(p - d) = f_K(p) - (a_K/p + b_K) d; (p/p_K)^z (1 - z d/p)
+                fl = tfma(-al, rel, tfma(-bl, d, fl));
+                fr = tfma(-ar, rel, tfma(-br, d, fr));
+                const T zr = K.z * rel;
+                if (positive(pzl)) pzl = tfma(-zr, pzl, pzl);
+                if (positive(pzr)) pzr = tfma(-zr, pzr, pzr);
             }
             p = pn;
             conv = true;
@@ -566,7 +601,7 @@ __device__ __forceinline__ Star<T> riemann_star(const Consts<T>& K, const Side<T
     }
     Star<T> st;
     st.p = p;
-    st.u = tfma(T(0.5), fr - fl, T(0.5) * (L.u + R.u));
+    st.u = T(0.5) * ((fr - fl) + (L.u + R.u));
     st.pzl = pzl;
     st.pzr = pzr;
     st.floored = floored;
@@ -637,14 +672,14 @@ __device__ __forceinline__ Prim<T> sample0(const Consts<T>& K, const Side<T>& L,
 // Physical flux along the normal of a primitive state.
 template <class T>
 __device__ __forceinline__ Cons<T> physical_flux(const Consts<T>& K, const Prim<T>& W) {
+    // E + p = rho |u|^2 / 2 + g/(g-1) p
     const T q2 = tfma(W.u, W.u, W.v * W.v);
-    const T E = tfma(T(0.5) * W.r, q2, W.p * K.inv_gm1);
     const T m = W.r * W.u;
     Cons<T> F;
     F.r = m;
     F.mn = tfma(m, W.u, W.p);
     F.mt = m * W.v;
-    F.E = W.u * (E + W.p);
+    F.E = W.u * tfma(T(0.5) * W.r, q2, W.p * K.g_gm1);
     return F;
 }
 
@@ -664,8 +699,9 @@ constexpr unsigned kEqualStateWork = 40u;
 // power far from p_K (exp2/log2) costs about four times the series near it.
 template <class T>
 __device__ __forceinline__ unsigned solve_work(const Consts<T>& K, const Star<T>& s) {
-    const unsigned pl = (s.pzl > T(0) && s.pzl < K.pz_series) ? 40u : 0u;
-    const unsigned pr = (s.pzr > T(0) && s.pzr < K.pz_series) ? 40u : 0u;
+    // (on the integer pipe in FP64: both operands of gt_pos are >= +0 there)
+    const unsigned pl = (positive(s.pzl) && gt_pos(K.pz_series, s.pzl)) ? 40u : 0u;
+    const unsigned pr = (positive(s.pzr) && gt_pos(K.pz_series, s.pzr)) ? 40u : 0u;
     return 140u + (unsigned)s.iters * (40u + pl + pr);
 }
 

@@ -35,7 +35,7 @@ Consts<T> make_consts(const hydro_params& p, double tol) {
     Consts<T> K;
     K.gamma = (T)g;
     K.gm1 = (T)(g - 1.0);
-    K.inv_gm1 = (T)(1.0 / (g - 1.0));
+    K.g_gm1 = (T)(g / (g - 1.0));
     K.z = (T)((g - 1.0) / (2.0 * g));
     K.zs = (T)((g + 1.0) / (2.0 * g));
     K.G3 = (T)(2.0 * g / (g - 1.0));
@@ -46,7 +46,6 @@ Consts<T> make_consts(const hydro_params& p, double tol) {
     K.inv_g = (T)(1.0 / g);
     K.hgp1 = (T)((g + 1.0) / 2.0);
     K.sqg = (T)std::sqrt(g);
-    K.isqg = (T)(1.0 / std::sqrt(g));
     K.rho_floor = (T)p.rho_floor;
     K.cf2g = (T)(p.c_floor * p.c_floor / g);
     K.pmin = (T)(p.rho_floor * (p.c_floor * p.c_floor / g));

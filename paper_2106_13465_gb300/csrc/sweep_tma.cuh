@@ -432,14 +432,15 @@ template <> struct MinBlocks<double, VAR_F64, DIR_X> { static constexpr int valu
 // LD = DIR_Y: the lines are columns (the y sweep, both precisions; chunk box
 // 32 columns x 4 rows).  LD = DIR_X: the lines are rows (the FP64 x sweep;
 // chunk box 4 columns x 32 rows, its x start s0 - 2 + 4c even, as a TMA copy
-// of FP64 needs).  The FP64 x sweep walks rather than taking segments
-// (sweep_x_kernel, which FP32 keeps): no cell is computed twice (a segment
-// computes 64 cells for 60 results) and each warp instruction of the solver
-// serves one interface per lane.
+// of FP64 needs: the tile start s0 is even).  The FP64 x sweep walks rather
+// than taking segments (sweep_x_kernel, which FP32 keeps): no cell is
+// computed twice (a segment computes 64 cells for 60 results) and each warp
+// instruction of the solver serves one interface per lane.
 template <class T>
 struct YWalk {
     Cons<T> u0, u1;   // conserved states at k-2, k-1
-    Prim<T> w0, w1;   // primitives at k-2, k-1
+    Prim<T> dl;       // primitives at k-1 minus those at k-2
+    Prim<T> w1;       // primitives at k-1
     T ir1;            // 1/rho at k-1
     Prim<T> wr0;      // right face of cell k-2
     Cons<T> flo;      // flux at (k-2) - 1/2
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
         const double dt = a.run[tile.grid].dt;
         const int n = (LD == DIR_Y) ? g.ny : g.nx, nlines = (LD == DIR_Y) ? g.nx : g.ny;
         if (tile.cell0 < 0 || tile.ncell < 1 || tile.cell0 + tile.ncell > n || tile.line0 < 0 ||
-            tile.line0 >= nlines || (tile.line0 & (kWarpLines - 1))) {
+            tile.line0 >= nlines || (tile.line0 & (kWarpLines - 1)) || (LD == DIR_X && (tile.cell0 & 1))) {
             kbad |= STATUS_BAD_TILE;  // never produced by the host or the tiler
             continue;
         }
@@ -569,11 +570,12 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
                 Cons<T> u = chunk_cell<T, LD>(sp, 0, lane);
                 if (kc < 0) u = walk_ghost<T, LD>(a.src, g, lsafe, kc, n, bclo, bchi, sp, kc, lane, w, gsave);
                 w.u0 = u;
-                w.w0 = cons_to_prim(K, u);
+                const Prim<T> w0 = cons_to_prim(K, u);
                 u = chunk_cell<T, LD>(sp, 1, lane);
                 if (kc + 1 < 0) u = walk_ghost<T, LD>(a.src, g, lsafe, kc + 1, n, bclo, bchi, sp, kc, lane, w, gsave);
                 w.u1 = u;
                 w.w1 = cons_to_prim(K, u, w.ir1);
+                w.dl = pdiff(w.w1, w0);
                 run = (Shortcuts<T>::stencil && same_bits(w.u1, w.u0)) ? 2 : 1;
                 j0 = 2;
             } else if (Shortcuts<T>::stencil && kc + C - 1 <= klast && kc + C - 1 < n &&
@@ -622,7 +624,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
                 const bool uniform = run >= 5 && k >= s0 + 2;
                 unsigned wk = kUniformWork;
                 T ir2;
-                Prim<T> w2, wr1;
+                Prim<T> w2, wr1, dr;
                 Cons<T> fhi;
                 if (!uniform) {
                     if (same) {  // the same conserved bits give the same primitives
@@ -631,8 +633,9 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
                     } else {
                         w2 = cons_to_prim(K, u, ir2);
                     }
+                    dr = pdiff(w2, w.w1);
                     Prim<T> wl1;
-                    trace<T, SV>(K, hdtdx, w.w0, w.w1, w.ir1, w2, wl1, wr1);  // cell k - 1
+                    trace<T, SV>(K, hdtdx, w.w1, w.ir1, w.dl, dr, wl1, wr1);  // cell k - 1
                     // at k = s0 the face left of cell s0-1 is not formed: solve
                     // a trivial problem (equal states) whose flux is never used
                     if (k == s0) w.wr0 = wl1;
@@ -640,10 +643,12 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
                 }
                 // the warp's work at this row is that of its slowest lane
                 if (kRecord) tcost += __reduce_max_sync(0xffffffffu, wk);
-                if (uniform) {  // the window rotates equal states
+                if (uniform) {  // the window rotates equal states (their
+                                // difference is +0, as computed for finite states)
                     w2 = w.w1;
                     ir2 = w.ir1;
                     wr1 = w.w1;
+                    dr = Prim<T>{T(0), T(0), T(0), T(0)};
                     fhi = w.flo;
                 }
                 if (k >= s0 + 2) {
@@ -663,7 +668,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
                 copied = uniform;
                 w.flo = fhi;
                 w.u0 = w.u1;
-                w.w0 = w.w1;
+                w.dl = dr;
                 w.wr0 = wr1;
                 w.u1 = u;
                 w.w1 = w2;
@@ -812,8 +817,9 @@ __device__ __forceinline__ void segment_update(const SweepArgs<T>& a, T dtdx, T 
     if (lane == 0) Wm = W0;
     if (lane == 31) Wp = W1;
     Prim<T> WLA, WRA, WLB, WRB;
-    trace<T, SV>(K, hdtdx, Wm, W0, ir0, W1, WLA, WRA);  // cell A
-    trace<T, SV>(K, hdtdx, W0, W1, ir1, Wp, WLB, WRB);  // cell B
+    const Prim<T> dAB = pdiff(W1, W0);  // right difference of A, left of B
+    trace<T, SV>(K, hdtdx, W0, ir0, pdiff(W0, Wm), dAB, WLA, WRA);  // cell A
+    trace<T, SV>(K, hdtdx, W1, ir1, dAB, pdiff(Wp, W1), WLB, WRB);  // cell B
     Prim<T> WRm = shfl_up1(WRB);  // right face of A-1
     if (lane == 0) WRm = WLA;
     const Cons<T> Fm = FluxOp<T, VAR, SV>::eval(a, WRm, WLA, r0, nfb, wk);  // A - 1/2
