@@ -109,6 +109,18 @@ template <class T>
 __host__ __device__ constexpr int sweep_smem_bytes(int dir) {
     return (kSweepThreads / 32) * ring_slots(dir) * (slot_bytes<T>(dir) + 8);
 }
+// The x walk (FP64): a ring of 2 chunk slots per warp (4 columns x 32 rows x
+// 4 planes each, as the y walk's slots), then, 128-byte aligned, 2 output
+// staging blocks of the same shape per warp, written to global memory by TMA.
+constexpr int kXWalkSlots = 2;
+template <class T>
+__host__ __device__ constexpr int xwalk_stage_offset() {
+    return ((kSweepThreads / 32) * kXWalkSlots * (slot_bytes<T>(DIR_Y) + 8) + 127) / 128 * 128;
+}
+template <class T>
+__host__ __device__ constexpr int xwalk_smem_bytes() {
+    return xwalk_stage_offset<T>() + (kSweepThreads / 32) * 2 * slot_bytes<T>(DIR_Y);
+}
 
 struct GridDesc {
     long long off;    // element offset of plane 0 in a state buffer

@@ -484,13 +484,16 @@ template <class T, int VAR, int WHICH, bool SV, int LD>
 __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
     sweep_walk_kernel(const SweepArgs<T> a) {
     constexpr int C = 4;
-    constexpr int S = ring_slots(DIR_Y);
+    // x: outputs staged in shared memory and stored by TMA (below)
+    constexpr bool kStage = (LD == DIR_X);
+    constexpr int S = kStage ? kXWalkSlots : ring_slots(DIR_Y);
     constexpr int SLOT = slot_bytes<T>(DIR_Y);
     constexpr int NWARPS = kSweepThreads / 32;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpRing<S, SLOT> ring;
     ring.init(smem, warp, NWARPS, lane);
+    T* const stage = reinterpret_cast<T*>(smem + xwalk_stage_offset<T>() + warp * 2 * SLOT);
 
     const Consts<T>& K = a.K;
     const unsigned acc = a.ctr->acc;
@@ -516,7 +519,8 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
         const double dt = a.run[tile.grid].dt;
         const int n = (LD == DIR_Y) ? g.ny : g.nx, nlines = (LD == DIR_Y) ? g.nx : g.ny;
         if (tile.cell0 < 0 || tile.ncell < 1 || tile.cell0 + tile.ncell > n || tile.line0 < 0 ||
-            tile.line0 >= nlines || (tile.line0 & (kWarpLines - 1)) || (LD == DIR_X && (tile.cell0 & 1))) {
+            tile.line0 >= nlines || (tile.line0 & (kWarpLines - 1)) ||
+            (kStage && ((tile.cell0 & 3) || ((tile.ncell & 3) && tile.cell0 + tile.ncell != n)))) {
             kbad |= STATUS_BAD_TILE;  // never produced by the host or the tiler
             continue;
         }
@@ -526,11 +530,17 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
         const int bclo = (LD == DIR_Y) ? g.bc[2] : g.bc[0], bchi = (LD == DIR_Y) ? g.bc[3] : g.bc[1];
         const int s0 = tile.cell0, s1 = tile.cell0 + tile.ncell;
         const int kfirst = s0 - 2, klast = s1 + 1;
-        const int nch = (klast - kfirst) / C + 1;
+        // chunk c holds positions kbase + 4c .. kbase + 4c + 3: y from
+        // kfirst; x from s0 - 4 (whole 32-byte row pieces, s0 being a
+        // multiple of 4), or from 0 at the grid's left end (the ghosts
+        // mirror cells of that chunk or wrap around)
+        const int kbase = kStage ? ((kfirst < 0) ? 0 : (kfirst & ~3)) : kfirst;
+        const int nch = (klast - kbase) / C + 1;
         const CUtensorMap* msrc = a.maps + map_index(tile.grid, a.src_buf, LD);
+        const CUtensorMap* mdst = a.maps + map_index(tile.grid, a.src_buf ^ 1, LD);
         auto issue = [&](int c) {
-            if (LD == DIR_Y) ring.issue(c % S, msrc, line0, kfirst + c * C);
-            else ring.issue(c % S, msrc, kfirst + c * C, line0);
+            if (LD == DIR_Y) ring.issue(c % S, msrc, line0, kbase + c * C);
+            else ring.issue(c % S, msrc, kbase + c * C, line0);
         };
         if (lane == 0)
             for (int c = 0; c < S && c < nch; ++c) issue(c);
@@ -545,6 +555,40 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
         T* __restrict__ qt = q0 + ((LD == DIR_Y) ? 1 : 2) * g.plane;
         T* __restrict__ qe = q0 + 3 * g.plane;
         const unsigned pitch = (LD == DIR_Y) ? (unsigned)g.pitch : 1u;
+        // Output cell q (warp-uniform) of this lane's line.  y: stored at
+        // once (a warp writes 32 consecutive cells).  x: a lane's cells are
+        // a row apart, so the warp collects 4 consecutive cells of its 32
+        // rows in a staging block (the layout of a chunk slot) and stores
+        // the block by TMA when it is full or holds the row's last cell;
+        // each block [s0 + 4b, s0 + 4b + 4) lies in the tile (or is clipped
+        // at the grid's right end and its last row), and a block's buffer
+        // is reused only after the store issued from it has read it.
+        auto emit = [&](int q, const Cons<T>& out) {
+            if constexpr (kStage) {
+                const int b = (q - s0) >> 2, col = (q - s0) & 3;
+                T* st = stage + (b & 1) * (SLOT / (int)sizeof(T));
+                st[(0 * 32 + lane) * C + col] = out.r;
+                st[(1 * 32 + lane) * C + col] = out.mn;
+                st[(2 * 32 + lane) * C + col] = out.mt;
+                st[(3 * 32 + lane) * C + col] = out.E;
+                if (col == 3 || q == s1 - 1) {
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_3d(mdst, s0 + 4 * b, line0, 0, st);
+                        bulk_commit();
+                        bulk_wait_read<1>();  // the other block's buffer is free again
+                    }
+                    __syncwarp();
+                }
+            } else if (valid) {
+                const unsigned o = (unsigned)q * pitch;
+                q0[o] = out.r;
+                qn[o] = out.mn;
+                qt[o] = out.mt;
+                qe[o] = out.E;
+            }
+        };
         YWalk<T> w = {};
         Cons<T> gsave = {};  // mirror of row n-2, kept for position n+1
         int run = 1;         // positions ending at the current one with equal conserved bits
@@ -562,22 +606,25 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
                 break;
             }
             const T* sp = reinterpret_cast<const T*>(ring.slot(sl));
-            const int kc = kfirst + c * C;
+            const int kc = kbase + c * C;
             int j0 = 0;
             if (c == 0) {
                 // positions s0-2 and s0-1 only fill the window (both < n - 1;
-                // below 0 they mirror rows of this chunk or wrap around)
-                Cons<T> u = chunk_cell<T, LD>(sp, 0, lane);
-                if (kc < 0) u = walk_ghost<T, LD>(a.src, g, lsafe, kc, n, bclo, bchi, sp, kc, lane, w, gsave);
+                // below 0 they mirror cells of this chunk or wrap around);
+                // jf = kfirst - kbase is 0 (y), 2 (x) or -2 (x, s0 = 0)
+                const int jf = kStage ? kfirst - kbase : 0;
+                Cons<T> u = (jf >= 0) ? chunk_cell<T, LD>(sp, jf, lane) : Cons<T>{};
+                if (kfirst < 0) u = walk_ghost<T, LD>(a.src, g, lsafe, kfirst, n, bclo, bchi, sp, kc, lane, w, gsave);
                 w.u0 = u;
                 const Prim<T> w0 = cons_to_prim(K, u);
-                u = chunk_cell<T, LD>(sp, 1, lane);
-                if (kc + 1 < 0) u = walk_ghost<T, LD>(a.src, g, lsafe, kc + 1, n, bclo, bchi, sp, kc, lane, w, gsave);
+                u = (jf >= 0) ? chunk_cell<T, LD>(sp, jf + 1, lane) : Cons<T>{};
+                if (kfirst + 1 < 0)
+                    u = walk_ghost<T, LD>(a.src, g, lsafe, kfirst + 1, n, bclo, bchi, sp, kc, lane, w, gsave);
                 w.u1 = u;
                 w.w1 = cons_to_prim(K, u, w.ir1);
                 w.dl = pdiff(w.w1, w0);
                 run = (Shortcuts<T>::stencil && same_bits(w.u1, w.u0)) ? 2 : 1;
-                j0 = 2;
+                j0 = jf + 2;
             } else if (Shortcuts<T>::stencil && kc + C - 1 <= klast && kc + C - 1 < n &&
                        __all_sync(0xffffffffu, !valid || copied)) {
                 // the previous row was a copy, so the window is the fixed
@@ -590,17 +637,8 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
 #pragma unroll
                 for (int j = 0; j < C; ++j) dif |= (unsigned long long)diff_bits(chunk_cell<T, LD>(sp, j, lane), w.u1);
                 if (__all_sync(0xffffffffu, !valid || dif == 0)) {
-                    if (valid) {
-                        const Cons<T> out = w.u0;
-#pragma unroll
-                        for (int j = 0; j < C; ++j) {
-                            const unsigned o = (unsigned)(kc + j - 2) * pitch;
-                            q0[o] = out.r;
-                            qn[o] = out.mn;
-                            qt[o] = out.mt;
-                            qe[o] = out.E;
-                        }
-                    }
+                    // (kc >= s0 + 3 here: a copy needs positions >= s0 + 2)
+                    for (int j = 0; j < C; ++j) emit(kc + j - 2, w.u0);
                     run += C;
                     if (kRecord) tcost += C * kUniformWork;
                     j0 = C;
@@ -654,16 +692,10 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
                 if (k >= s0 + 2) {
                     Cons<T> out = w.u0;
                     if (!uniform) out = update(w.u0, dtdx, fhi, w.flo);
-                    if (valid) {
-                        const unsigned o = (unsigned)(k - 2) * pitch;
-                        q0[o] = out.r;
-                        qn[o] = out.mn;
-                        qt[o] = out.mt;
-                        qe[o] = out.E;
-                        // a copy equal to the previous row's copy has its
-                        // status and wave speed already counted
-                        if (!(uniform && copied)) check_cell<T, WHICH>(K, out, tbad, smax, sbits);
-                    }
+                    emit(k - 2, out);
+                    // a copy equal to the previous row's copy has its status
+                    // and wave speed already counted
+                    if (valid && !(uniform && copied)) check_cell<T, WHICH>(K, out, tbad, smax, sbits);
                 }
                 copied = uniform;
                 w.flo = fhi;
@@ -679,6 +711,11 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
                 fence_proxy_async_smem();
                 issue(c + S);
             }
+        }
+        if constexpr (kStage) {
+            // the staging blocks are read before the next tile writes them
+            if (lane == 0) bulk_wait_read<0>();
+            __syncwarp();
         }
         if (aborted) break;
         if (kRecord && a.ycost && lane == 0) {
@@ -702,6 +739,9 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
     if (aborted && lane == 0) {
         atomicOr(&a.ctr->status, STATUS_TIMEOUT);
         ring.drain();
+    }
+    if constexpr (kStage) {
+        if (lane == 0) bulk_wait<0>();  // this warp's stores have completed
     }
     for (int o = 16; o > 0; o >>= 1) {
         nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
@@ -1001,7 +1041,8 @@ struct KernelOf {
 // Dynamic shared memory of a sweep launch (a walker's ring holds chunks).
 template <class T, int DIR>
 constexpr int launch_smem_bytes() {
-    return sweep_smem_bytes<T>((DIR == DIR_X && !x_walks<T>()) ? DIR_X : DIR_Y);
+    if constexpr (DIR == DIR_X) return x_walks<T>() ? xwalk_smem_bytes<T>() : sweep_smem_bytes<T>(DIR_X);
+    return sweep_smem_bytes<T>(DIR_Y);
 }
 
 // Whether the constants select a scheme variant (the kernels compiled with
