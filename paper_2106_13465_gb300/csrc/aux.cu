@@ -22,7 +22,10 @@ __global__ void step_prologue_kernel(GridRun* run, const GridDesc* grids, int ng
         run[g].smax32 = 0u;
         if (dt_log) dt_log[g] = dt;
     }
-    for (int i = threadIdx.x; i < kMaxSmIds; i += blockDim.x) ctr->sm_slot[i] = 0u;
+    for (int i = threadIdx.x; i < kMaxSmIds; i += blockDim.x) {
+        ctr->sm_slot[0][i] = 0u;
+        ctr->sm_slot[1][i] = 0u;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         ctr->acc = dst;
@@ -32,8 +35,10 @@ __global__ void step_prologue_kernel(GridRun* run, const GridDesc* grids, int ng
         ctr->redo_count[1] = 0u;
         ctr->redo_claim[0] = 0u;
         ctr->redo_claim[1] = 0u;
-        ctr->ytiles[0] = 0u;
-        ctr->ytiles[1] = 0u;
+        ctr->wtiles[0][0] = 0u;
+        ctr->wtiles[0][1] = 0u;
+        ctr->wtiles[1][0] = 0u;
+        ctr->wtiles[1][1] = 0u;
         ctr->steps += 1ull;
     }
 }
@@ -46,10 +51,10 @@ cudaError_t launch_step_prologue(GridRun* run, const GridDesc* grids, int ngrids
     return cudaGetLastError();
 }
 
-// ---- adaptive y tiles ------------------------------------------------------
+// ---- adaptive walk tiles (FP64 x and y) ------------------------------------
 // One thread per tile of the static tiling (the tiling the scheduling model
 // picks for uniform cost; every tile a whole number of cost blocks except at
-// the end of a column).  The thread walks the tile's blocks in order and
+// the end of a line).  The thread walks the tile's blocks in order and
 // starts a new piece before block b when adding b would take the piece's
 // recorded work above `cap` (a piece always gets at least one block), so
 // uniform work reproduces the static tiling and the tiles where the solver
@@ -57,12 +62,14 @@ cudaError_t launch_step_prologue(GridRun* run, const GridDesc* grids, int ngrids
 // (from the front of the list), the others last (from its back): the warps
 // start on the long jobs and the short ones fill the tail of the sweep.
 // Each warp reserves its threads' slots with one atomic per class.  The
-// previous step's y sweep recorded the work and its total (in the slot of
-// its step parity); this kernel clears the slot the coming y sweep fills.
+// previous step's sweep in the same direction recorded the work and its
+// total (in the slot of its step parity); this kernel clears the slot the
+// coming sweep fills.  A piece starts on a cost block (of blk cells).
 template <bool EMIT>
-__device__ __forceinline__ void split_tile(const Tile& st, const float* __restrict__ cst, float cap, float big,
-                                           Tile* __restrict__ out, int cap_tiles, unsigned& nf, unsigned& nb) {
-    const int b0 = st.cell0 / kYBlock, b1 = (st.cell0 + st.ncell + kYBlock - 1) / kYBlock;
+__device__ __forceinline__ void split_tile(const Tile& st, const float* __restrict__ cst, int blk, float cap,
+                                           float big, Tile* __restrict__ out, int cap_tiles, unsigned& nf,
+                                           unsigned& nb) {
+    const int b0 = st.cell0 / blk, b1 = (st.cell0 + st.ncell + blk - 1) / blk;
     const int rend = st.cell0 + st.ncell;
     float acc = 0.0f;
     int start = b0;
@@ -78,13 +85,13 @@ __device__ __forceinline__ void split_tile(const Tile& st, const float* __restri
     for (int b = b0; b < b1; ++b) {
         const float c = cst[b];
         if (b > start && acc + c > cap) {
-            put(start * kYBlock, (b - start) * kYBlock, acc);
+            put(start * blk, (b - start) * blk, acc);
             acc = 0.0f;
             start = b;
         }
         acc += c;
     }
-    put(start * kYBlock, rend - start * kYBlock, acc);
+    put(start * blk, rend - start * blk, acc);
 }
 
 __device__ __forceinline__ unsigned warp_exclusive_scan(unsigned v, int lane, unsigned& total) {
@@ -97,18 +104,18 @@ __device__ __forceinline__ unsigned warp_exclusive_scan(unsigned v, int lane, un
     return incl - v;
 }
 
-__global__ void retile_y_kernel(const GridDesc* __restrict__ grids, const Tile* __restrict__ stat, int nstat,
-                                const float* __restrict__ ycost, DevCounters* ctr, Tile* __restrict__ tiles,
-                                int cap_tiles, double cap_per_total, double big_per_total,
-                                double big_of_max) {
+__global__ void retile_kernel(int dir, const GridDesc* __restrict__ grids, const Tile* __restrict__ stat,
+                              int nstat, const float* __restrict__ wcost, DevCounters* ctr,
+                              Tile* __restrict__ tiles, int cap_tiles, double cap_per_total,
+                              double big_per_total, double big_of_max) {
     const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int lane = threadIdx.x & 31;
     const unsigned par = (unsigned)(ctr->steps & 1ull);
-    const double total = (double)ctr->ycost_total[par ^ 1u];
-    const double bmax = big_of_max * (double)ctr->ycost_max[par ^ 1u];
+    const double total = (double)ctr->wcost_total[dir][par ^ 1u];
+    const double bmax = big_of_max * (double)ctr->wcost_max[dir][par ^ 1u];
     if (i == 0) {
-        ctr->ycost_total[par] = 0ull;
-        ctr->ycost_max[par] = 0u;
+        ctr->wcost_total[dir][par] = 0ull;
+        ctr->wcost_max[dir][par] = 0u;
     }
     const float cap = (float)(total * cap_per_total);
     const float big = (float)fmax(total * big_per_total, bmax);
@@ -118,29 +125,29 @@ __global__ void retile_y_kernel(const GridDesc* __restrict__ grids, const Tile* 
     if (i < nstat) {
         st = stat[i];
         const GridDesc& g = grids[st.grid];
-        cst = ycost + g.yblk + (long long)(st.line0 / kWarpLines) * g.nrb;
-        split_tile<false>(st, cst, cap, big, tiles, cap_tiles, nf, nb);
+        cst = wcost + g.wblk[dir] + (long long)(st.line0 / kWarpLines) * g.wnb[dir];
+        split_tile<false>(st, cst, walk_block(dir), cap, big, tiles, cap_tiles, nf, nb);
     }
     // warp-aggregated reservation of the pieces' slots, one atomic per class
     unsigned tf, tb;
     const unsigned of = warp_exclusive_scan(nf, lane, tf), ob = warp_exclusive_scan(nb, lane, tb);
     unsigned basef = 0, baseb = 0;
     if (lane == 0) {
-        basef = atomicAdd(&ctr->ytiles[0], tf);
-        baseb = atomicAdd(&ctr->ytiles[1], tb);
+        basef = atomicAdd(&ctr->wtiles[dir][0], tf);
+        baseb = atomicAdd(&ctr->wtiles[dir][1], tb);
     }
     basef = __shfl_sync(0xffffffffu, basef, 0) + of;
     baseb = __shfl_sync(0xffffffffu, baseb, 0) + ob;
-    if (i < nstat) split_tile<true>(st, cst, cap, big, tiles, cap_tiles, basef, baseb);
+    if (i < nstat) split_tile<true>(st, cst, walk_block(dir), cap, big, tiles, cap_tiles, basef, baseb);
 }
 
-cudaError_t launch_retile_y(const GridDesc* grids, const Tile* stat, int nstat, const float* ycost,
-                            DevCounters* ctr, Tile* tiles, int cap_tiles, double cap_per_total,
-                            double big_per_total, double big_of_max, cudaStream_t s) {
+cudaError_t launch_retile(int dir, const GridDesc* grids, const Tile* stat, int nstat, const float* wcost,
+                          DevCounters* ctr, Tile* tiles, int cap_tiles, double cap_per_total,
+                          double big_per_total, double big_of_max, cudaStream_t s) {
     const int threads = 128;
     const int blocks = (nstat + threads - 1) / threads;
-    retile_y_kernel<<<blocks, threads, 0, s>>>(grids, stat, nstat, ycost, ctr, tiles, cap_tiles, cap_per_total,
-                                               big_per_total, big_of_max);
+    retile_kernel<<<blocks, threads, 0, s>>>(dir, grids, stat, nstat, wcost, ctr, tiles, cap_tiles, cap_per_total,
+                                             big_per_total, big_of_max);
     return cudaGetLastError();
 }
 

@@ -342,7 +342,8 @@ __global__ void __launch_bounds__(kFusedThreads, (FusedMinBlocks<T, VAR>::value)
             __syncthreads();
             if (threadIdx.x == 0) {
                 a.tile_smax[t] = s_sbits;
-                if (s_sbits) atomicMax(&a.run[tile.grid].smax32, s_sbits);
+                // (the maximum only grows: most tiles skip the atomic)
+                if (s_sbits && s_sbits > __ldcg(&a.run[tile.grid].smax32)) atomicMax(&a.run[tile.grid].smax32, s_sbits);
             }
         } else {
             double m = (double)acc.smax;
@@ -350,7 +351,9 @@ __global__ void __launch_bounds__(kFusedThreads, (FusedMinBlocks<T, VAR>::value)
                 const double v = __shfl_xor_sync(0xffffffffu, m, o);
                 m = (v <= m) ? m : v;
             }
-            if (lane == 0) atomicMax(&a.run[tile.grid].wmax[accslot], (unsigned long long)__double_as_longlong(m));
+            const unsigned long long mb = (unsigned long long)__double_as_longlong(m);
+            if (lane == 0 && mb > __ldcg(&a.run[tile.grid].wmax[accslot]))
+                atomicMax(&a.run[tile.grid].wmax[accslot], mb);
         }
     }
 

@@ -101,15 +101,16 @@ struct hydro_ctx {
     size_t dt_log_cap = 0;
     CUtensorMap* d_maps = nullptr;  // [grid][buffer][dir]
     int* d_redo = nullptr;          // [2][redo_cap] FP32 second-pass tile lists
-    float* d_ycost = nullptr;       // recorded y-sweep cost per block (adaptive y tiles)
-    unsigned long long* d_yclaim = nullptr;  // claim words of the adaptive y tiles
-    Tile* d_ystat = nullptr;        // static y tiling the adaptive tiles split
+    // adaptive walk tiles (FP64), per walk direction d (0 x, 1 y)
+    float* d_wcost[2] = {nullptr, nullptr};               // recorded cost per block
+    unsigned long long* d_wclaim[2] = {nullptr, nullptr};  // claim words of the long jobs
+    Tile* d_wstat[2] = {nullptr, nullptr};                 // static tiling the pieces split
     unsigned int* d_tile_smax = nullptr;  // FP64: max speed estimate per tile of a second sweep
     int tile_smax_cap = 0;
-    int nystat = 0;
-    long long nyblocks = 0;         // cost blocks of all grids
-    bool y_adaptive = false;        // y tiles cut from recorded costs every step
-    double y_cap = 0.0;             // adaptive y tiles: cost cap / total recorded cost
+    int nwstat[2] = {0, 0};
+    long long nwblocks[2] = {0, 0};         // cost blocks of all grids
+    bool w_adaptive[2] = {false, false};    // tiles cut from recorded costs every step
+    double w_cap[2] = {0.0, 0.0};           // cost cap / total recorded cost
     int redo_cap = 0;
     int ctas_redo[3] = {0, 0, 0};
     hydro_tuning tuning{kDefaultTileLen, 0, kDefaultGraphSteps, 0, 0};
@@ -260,7 +261,7 @@ double list_schedule_makespan(const std::vector<Tile>& tiles, int dir, int warps
 int auto_tile_len(const std::vector<GridDesc>& gd, int dir, int warps, bool xwalk = false) {
     std::vector<int> cand;
     if (dir == DIR_Y || xwalk) {
-        for (int L = 16; L <= 128; L += 4) cand.push_back(L);
+        for (int L = 4; L <= 128; L += 4) cand.push_back(L);
         for (int L : {160, 192, 256, 384, 512}) cand.push_back(L);
     } else {
         for (int L : {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 48, 64, 128}) cand.push_back(L);
@@ -317,24 +318,28 @@ hydro_status build_tensor_maps(hydro_ctx* c) {
     return HYDRO_OK;
 }
 
-// Cost blocks before any y sweep has run: the rows each block holds (a
+// Cost blocks before any sweep has run: the cells each block holds (a
 // uniform cost per cell), and the same total in both parity slots.
-hydro_status init_ycost(hydro_ctx* c) {
-    std::vector<float> cost((size_t)c->nyblocks);
-    unsigned long long total = 0;
-    for (int g = 0; g < (int)c->gd.size(); ++g) {
-        const GridDesc& d = c->gd[g];
-        for (int cg = 0; cg < d.ycg; ++cg) {
-            for (int b = 0; b < d.nrb; ++b) {
-                const int rows = std::min(kYBlock, d.ny - b * kYBlock);
-                cost[(size_t)(d.yblk + (long long)cg * d.nrb + b)] = (float)rows;
-                total += (unsigned long long)rows;
+hydro_status init_wcost(hydro_ctx* c) {
+    for (int dir = 0; dir < 2; ++dir) {
+        std::vector<float> cost((size_t)c->nwblocks[dir]);
+        unsigned long long total = 0;
+        const int B = walk_block(dir);
+        for (int g = 0; g < (int)c->gd.size(); ++g) {
+            const GridDesc& d = c->gd[g];
+            const int n = dir == DIR_X ? d.nx : d.ny;
+            for (int lg = 0; lg < d.wlg[dir]; ++lg) {
+                for (int b = 0; b < d.wnb[dir]; ++b) {
+                    const int cells = std::min(B, n - b * B);
+                    cost[(size_t)(d.wblk[dir] + (long long)lg * d.wnb[dir] + b)] = (float)cells;
+                    total += (unsigned long long)cells;
+                }
             }
         }
+        const unsigned long long tot2[2] = {total, total};
+        HCK(c, cudaMemcpy(c->d_wcost[dir], cost.data(), sizeof(float) * cost.size(), cudaMemcpyHostToDevice));
+        HCK(c, cudaMemcpy(&c->d_ctr->wcost_total[dir][0], tot2, sizeof tot2, cudaMemcpyHostToDevice));
     }
-    const unsigned long long tot2[2] = {total, total};
-    HCK(c, cudaMemcpy(c->d_ycost, cost.data(), sizeof(float) * cost.size(), cudaMemcpyHostToDevice));
-    HCK(c, cudaMemcpy(&c->d_ctr->ycost_total[0], tot2, sizeof tot2, cudaMemcpyHostToDevice));
     return HYDRO_OK;
 }
 
@@ -350,34 +355,35 @@ hydro_status upload_tiles(hydro_ctx* c) {
         const int chosen = d == DIR_X ? c->tuning.span_len / kXStride : c->tuning.tile_len;
         if (c->d_tiles[d]) cudaFree(c->d_tiles[d]);
         c->d_tiles[d] = nullptr;
-        if (d == DIR_Y && chosen == 0 && c->prec == 64) {
-            // adaptive y tiles (FP64, where the cost of a cell varies most
+        if (chosen == 0 && c->prec == 64) {
+            // adaptive walk tiles (FP64, where the cost of a cell varies most
             // with the Riemann problems it meets): the list is cut on the
-            // device every step; it
-            // never holds more tiles than there are cost blocks.  The length
-            // cap is the model's static tile length; the cost cap a multiple
-            // of the mean cost of such a tile.
-            const int L = auto_tile_len(c->gd, d, resident_warps);
-            const int lb = std::max(kYBlock, L / kYBlock * kYBlock);  // L is a multiple of 4
+            // device every step; it never holds more tiles than there are
+            // cost blocks.  The length cap is the model's static tile length;
+            // the cost cap a multiple of the mean cost of such a tile.
+            const bool xwalk = d == DIR_X;
+            const int B = walk_block(d);
+            const int L = auto_tile_len(c->gd, d, resident_warps, xwalk);
+            const int lb = std::max(B, L / B * B);  // L is a multiple of 4
             std::vector<Tile> t;
-            build_tiles(c->gd, d, lb, t);
-            if (c->d_ystat) cudaFree(c->d_ystat);
-            c->d_ystat = nullptr;
-            HCK(c, cudaMalloc(&c->d_ystat, sizeof(Tile) * t.size()));
-            HCK(c, cudaMemcpy(c->d_ystat, t.data(), sizeof(Tile) * t.size(), cudaMemcpyHostToDevice));
-            c->nystat = (int)t.size();
-            c->y_adaptive = true;
-            c->y_cap = kYCostCap / (double)t.size();
+            build_tiles(c->gd, d, lb, t, xwalk);
+            if (c->d_wstat[d]) cudaFree(c->d_wstat[d]);
+            c->d_wstat[d] = nullptr;
+            HCK(c, cudaMalloc(&c->d_wstat[d], sizeof(Tile) * t.size()));
+            HCK(c, cudaMemcpy(c->d_wstat[d], t.data(), sizeof(Tile) * t.size(), cudaMemcpyHostToDevice));
+            c->nwstat[d] = (int)t.size();
+            c->w_adaptive[d] = true;
+            c->w_cap[d] = kYCostCap / (double)t.size();
             c->tile_len_used[d] = 0;
-            HCK(c, cudaMalloc(&c->d_tiles[d], sizeof(Tile) * (size_t)c->nyblocks));
-            c->ntiles[d] = (int)std::min<long long>(c->nyblocks, 1LL << 30);
+            HCK(c, cudaMalloc(&c->d_tiles[d], sizeof(Tile) * (size_t)c->nwblocks[d]));
+            c->ntiles[d] = (int)std::min<long long>(c->nwblocks[d], 1LL << 30);
             // claim words start below every step count (steps count from 1)
-            if (c->d_yclaim) cudaFree(c->d_yclaim);
-            c->d_yclaim = nullptr;
-            HCK(c, cudaMalloc(&c->d_yclaim, sizeof(unsigned long long) * (size_t)c->nyblocks));
-            HCK(c, cudaMemset(c->d_yclaim, 0, sizeof(unsigned long long) * (size_t)c->nyblocks));
+            if (c->d_wclaim[d]) cudaFree(c->d_wclaim[d]);
+            c->d_wclaim[d] = nullptr;
+            HCK(c, cudaMalloc(&c->d_wclaim[d], sizeof(unsigned long long) * (size_t)c->nwblocks[d]));
+            HCK(c, cudaMemset(c->d_wclaim[d], 0, sizeof(unsigned long long) * (size_t)c->nwblocks[d]));
         } else {
-            if (d == DIR_Y) c->y_adaptive = false;
+            c->w_adaptive[d] = false;
             // FP64 walks the x lines: span_len (a multiple of 60, so of 4) is
             // then the cells of a walk
             const bool xwalk = d == DIR_X && c->prec == 64;
@@ -460,9 +466,9 @@ SweepArgs<T> sweep_args(hydro_ctx* c, int which, const Consts<T>& K) {
     a.ntiles = 0;
     a.ngrids = (int)c->gd.size();
     a.ntiles_dev = nullptr;
-    a.yclaim = nullptr;
+    a.wclaim = nullptr;
     a.nsm = c->nsm;
-    a.ycost = c->d_ycost;
+    a.wcost = nullptr;
     a.tile_smax = c->d_tile_smax;
     a.wait_limit = c->wait_limit;
     a.which = which;
@@ -518,9 +524,10 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
     e = launch_step_prologue(c->d_run, c->d_grids, (int)c->gd.size(), c->d_ctr, ovr, c->cfl, log, s);
     if (e != cudaSuccess) return e;
-    if (c->y_adaptive) {
-        e = launch_retile_y(c->d_grids, c->d_ystat, c->nystat, c->d_ycost, c->d_ctr, c->d_tiles[DIR_Y],
-                            c->ntiles[DIR_Y], c->y_cap, c->y_cap * (kYBigJob / kYCostCap), kYBigOfMax, s);
+    for (int d = 0; d < 2; ++d) {
+        if (!c->w_adaptive[d]) continue;
+        e = launch_retile(d, c->d_grids, c->d_wstat[d], c->nwstat[d], c->d_wcost[d], c->d_ctr, c->d_tiles[d],
+                          c->ntiles[d], c->w_cap[d], c->w_cap[d] * (kYBigJob / kYCostCap), kYBigOfMax, s);
         if (e != cudaSuccess) return e;
     }
     if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
@@ -530,9 +537,10 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
         SweepArgs<T> a = sweep_args<T>(c, which, K);
         a.tiles = c->d_tiles[dir];
         a.ntiles = c->ntiles[dir];
-        if (dir == DIR_Y && c->y_adaptive) {
-            a.ntiles_dev = c->d_ctr->ytiles;
-            a.yclaim = c->d_yclaim;
+        if (sizeof(T) == 8) a.wcost = c->d_wcost[dir];
+        if (c->w_adaptive[dir]) {
+            a.ntiles_dev = c->d_ctr->wtiles[dir];
+            a.wclaim = c->d_wclaim[dir];
         }
         if (sizeof(T) == 8) {
             e = launch_sweep<T>(dir, VAR_F64, a, c->ctas[dir], s);
@@ -557,7 +565,7 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
 // fused step: the prologue, the step kernel and the CFL or second pass.
 int launches_per_step(const hydro_ctx* c) {
     if (c->tuning.fused) return 3;
-    return 1 + (c->y_adaptive ? 1 : 0) + (c->prec == 64 ? 2 + 1 : 2 * 2);
+    return 1 + (c->w_adaptive[0] ? 1 : 0) + (c->w_adaptive[1] ? 1 : 0) + (c->prec == 64 ? 2 + 1 : 2 * 2);
 }
 
 cudaError_t enqueue_step(hydro_ctx* c, int parity, const double* ovr, double* log, cudaStream_t s,
@@ -664,10 +672,13 @@ hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
         d.off = off;
         for (int k = 0; k < 4; ++k) d.bc[k] = G.bc[k];
         d.h = G.h;
-        d.ycg = (G.nx + kWarpLines - 1) / kWarpLines;
-        d.nrb = (G.ny + kYBlock - 1) / kYBlock;
-        d.yblk = c->nyblocks;
-        c->nyblocks += (long long)d.ycg * d.nrb;
+        for (int dir = 0; dir < 2; ++dir) {
+            const int nlines = dir == DIR_X ? G.ny : G.nx, ncells = dir == DIR_X ? G.nx : G.ny;
+            d.wlg[dir] = (nlines + kWarpLines - 1) / kWarpLines;
+            d.wnb[dir] = (ncells + walk_block(dir) - 1) / walk_block(dir);
+            d.wblk[dir] = c->nwblocks[dir];
+            c->nwblocks[dir] += (long long)d.wlg[dir] * d.wnb[dir];
+        }
         off = round_up(off + 4 * d.plane, align_elems);
         max_cells = std::max(max_cells, (long long)G.nx * G.ny);
         max_ny = std::max(max_ny, (long long)G.ny);
@@ -705,7 +716,9 @@ hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
     if (c->prec == 32 &&
         (st = alloc((void**)&c->d_stage, sizeof(double) * 4 * max_cells, "staging")) != HYDRO_OK)
         return bail(st);
-    if ((st = alloc((void**)&c->d_ycost, sizeof(float) * c->nyblocks, "y cost blocks")) != HYDRO_OK) return bail(st);
+    for (int dir = 0; dir < 2; ++dir)
+        if ((st = alloc((void**)&c->d_wcost[dir], sizeof(float) * c->nwblocks[dir], "cost blocks")) != HYDRO_OK)
+            return bail(st);
     e = cudaMemcpy(c->d_grids, c->gd.data(), sizeof(GridDesc) * c->gd.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_run, 0, sizeof(GridRun) * c->gd.size());
     if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, sizeof(DevCounters));
@@ -713,7 +726,7 @@ hydro_status hydro_init(const hydro_params* params, hydro_ctx** out) {
     if (e == cudaSuccess) e = cudaMemset(c->buf[1], 0, c->buf_elems * c->esz);
     if (e != cudaSuccess) { fail_cuda(c, "context set-up", e); return bail(HYDRO_ECUDA); }
     if ((st = build_tensor_maps(c)) != HYDRO_OK) return bail(st);
-    if ((st = init_ycost(c)) != HYDRO_OK) return bail(st);
+    if ((st = init_wcost(c)) != HYDRO_OK) return bail(st);
     if ((st = upload_tiles(c)) != HYDRO_OK) return bail(st);
 
     *out = c;
@@ -736,9 +749,11 @@ void hydro_destroy(hydro_ctx* c) {
     cudaFree(c->d_dt_log);
     cudaFree(c->d_maps);
     cudaFree(c->d_redo);
-    cudaFree(c->d_ycost);
-    cudaFree(c->d_yclaim);
-    cudaFree(c->d_ystat);
+    for (int dir = 0; dir < 2; ++dir) {
+        cudaFree(c->d_wcost[dir]);
+        cudaFree(c->d_wclaim[dir]);
+        cudaFree(c->d_wstat[dir]);
+    }
     cudaFree(c->d_tile_smax);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

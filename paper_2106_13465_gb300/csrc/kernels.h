@@ -71,9 +71,13 @@ enum { VAR_F64 = 0, VAR_F32_MAIN = 1, VAR_F32_REDO = 2 };
 
 constexpr int kWarpLines = 32;      // lines per warp tile (one per lane)
 constexpr int kYBlock = 1;          // rows per cost block of the adaptive y tiles
-constexpr double kYCostCap = 1.0;   // adaptive y tile work cap / mean static tile work
-constexpr double kYBigJob = 0.5;    // adaptive y tiles queued first: work / mean static tile work
-constexpr double kYBigOfMax = 0.5;  // ... and work / largest piece of the previous y sweep
+constexpr int kXBlock = 4;          // columns per cost block of the adaptive x tiles (FP64
+                                    // x walks start and end on multiples of 4 columns)
+constexpr double kYCostCap = 1.0;   // adaptive tile work cap / mean static tile work
+constexpr double kYBigJob = 0.5;    // adaptive tiles queued first: work / mean static tile work
+constexpr double kYBigOfMax = 0.5;  // ... and work / largest piece of the previous sweep
+// cells per cost block of the adaptive tiles of walk direction d
+__host__ __device__ constexpr int walk_block(int d) { return d == 0 ? kXBlock : kYBlock; }
 constexpr int kSweepThreads = 128;  // threads per CTA of the sweep kernels
 // polls of an mbarrier before a sweep warp gives up waiting for a TMA copy
 // (the default of SweepArgs::wait_limit, and the bound of the wait for the
@@ -128,8 +132,11 @@ struct GridDesc {
     int nx, ny, pitch;
     int bc[4];        // x low, x high, y low, y high
     double h;
-    long long yblk;   // first cost block of the grid (adaptive y tiles)
-    int ycg, nrb;     // column groups ceil(nx/32), row blocks ceil(ny/kYBlock)
+    // adaptive walk tiles, per walk direction d (0 x, 1 y): the grid's first
+    // cost block, its line groups of 32 (x: rows, y: columns) and the cost
+    // blocks of walk_block(d) cells along a line group
+    long long wblk[2];
+    int wlg[2], wnb[2];
 };
 
 // A warp tile: lines [line0, line0 + 32) of grid `grid`, cells
@@ -149,7 +156,7 @@ struct GridRun {
 };
 
 
-// SM ids below this bound spread the long adaptive y tiles (see claim_tile).
+// SM ids below this bound spread the long adaptive tiles (see claim_tile).
 constexpr int kMaxSmIds = 256;
 
 // Context-wide device counters.
@@ -161,12 +168,13 @@ struct DevCounters {
     unsigned int redo_claim[2];  // work counters of the second pass
     unsigned long long steps;
     unsigned long long riemann_fp64;
-    unsigned int ytiles[2];               // adaptive y tiles of the current step: the
-                                          // list holds ytiles[0] long jobs from its
-                                          // front and ytiles[1] short ones from its back
-    unsigned long long ycost_total[2];    // recorded y-sweep work, by step parity
-    unsigned int ycost_max[2];            // largest recorded work of a y tile, by step parity
-    unsigned int sm_slot[kMaxSmIds];      // y sweep: warps that have started on each SM
+    unsigned int wtiles[2][2];            // adaptive tiles of walk direction d in the
+                                          // current step: the list holds wtiles[d][0]
+                                          // long jobs from its front and wtiles[d][1]
+                                          // short ones from its back
+    unsigned long long wcost_total[2][2]; // recorded work of direction d, by step parity
+    unsigned int wcost_max[2][2];         // largest recorded tile work, by step parity
+    unsigned int sm_slot[2][kMaxSmIds];   // per sweep of the step: warps started on each SM
     int wait_site;                        // the first wait that gave up: kernel (1 x, 2 y,
     int wait_tile;                        // 3 fused, 4 fused second pass) and its tile
 };
@@ -180,12 +188,12 @@ struct SweepArgs {
     const CUtensorMap* maps;
     int ntiles;
     int ngrids;
-    const unsigned int* ntiles_dev;  // adaptive y tiles: the two counts on the device
+    const unsigned int* ntiles_dev;  // adaptive tiles: the two counts on the device
                                      // (ntiles is then the capacity of the list)
-    unsigned long long* yclaim;      // adaptive y tiles: step count at which each long
+    unsigned long long* wclaim;      // adaptive tiles: step count at which each long
                                      // job was last claimed (each taken once per step)
     int nsm;                         // SMs of the device
-    float* ycost;                    // y sweep: per-block work recorded here
+    float* wcost;                    // FP64 walks: per-block work recorded here
     unsigned int* tile_smax;         // FP64 second sweep: max FP32 speed estimate per tile
     unsigned wait_limit;  // polls of a TMA completion before a warp gives up
     int which;       // 0: first sweep of the step, 1: second (folds in CFL max)
@@ -241,15 +249,15 @@ cudaError_t launch_fused(int order, int var, const SweepArgs<T>& a, int nctas, c
 template <class T>
 int fused_ctas_per_sm(int var);
 
-// Cut the adaptive y tiles from the recorded work: each of the nstat tiles
-// of the static tiling `stat` (whole cost blocks) is split where its pieces'
-// work would exceed cap_per_total times the total recorded work of the
-// previous y sweep; pieces of at least big_per_total times that total and
-// big_of_max times the largest tile work it recorded are queued first, the
-// rest last (list of cap_tiles slots).
-cudaError_t launch_retile_y(const GridDesc* grids, const Tile* stat, int nstat, const float* ycost,
-                            DevCounters* ctr, Tile* tiles, int cap_tiles, double cap_per_total,
-                            double big_per_total, double big_of_max, cudaStream_t s);
+// Cut the adaptive tiles of walk direction dir from the recorded work: each
+// of the nstat tiles of the static tiling `stat` (whole cost blocks) is
+// split where its pieces' work would exceed cap_per_total times the total
+// recorded work of the previous sweep in that direction; pieces of at least
+// big_per_total times that total and big_of_max times the largest tile work
+// it recorded are queued first, the rest last (list of cap_tiles slots).
+cudaError_t launch_retile(int dir, const GridDesc* grids, const Tile* stat, int nstat, const float* wcost,
+                          DevCounters* ctr, Tile* tiles, int cap_tiles, double cap_per_total,
+                          double big_per_total, double big_of_max, cudaStream_t s);
 
 cudaError_t launch_step_prologue(GridRun* run, const GridDesc* grids, int ngrids,
                                  DevCounters* ctr, const double* dt_override, double cfl,

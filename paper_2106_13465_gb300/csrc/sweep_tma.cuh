@@ -299,8 +299,8 @@ __device__ __forceinline__ void record_wait_site(DevCounters* ctr, int site, int
 // Claim the next tile: the main pass takes the work list in order, the FP32
 // second pass takes the tiles the main pass queued.  -1 when none is left.
 //
-// Adaptive y tiles (FP64): long jobs from the front of the list, then short
-// ones from its back.  The long jobs are the few rows of heavy Riemann
+// Adaptive walk tiles (FP64): long jobs from the front of the list, then
+// short ones from its back.  The long jobs are the few rows of heavy Riemann
 // problems of a sweep, and two of them in one SM sub-partition halve each
 // other's FP64 rate, so a warp's first claim spreads them over the SMs: the
 // s-th warp to start on SM m takes long job s * nsm + m, if nobody has.  Every long job also stays in the counter's
@@ -317,20 +317,20 @@ __device__ __forceinline__ int claim_tile(const SweepArgs<T>& a, int lane, bool 
             t = (i < a.ctr->redo_count[a.which]) ? a.redo_list[a.which * a.redo_cap + i] : -1;
         } else if (a.ntiles_dev) {
             const unsigned nf = a.ntiles_dev[0], nb = a.ntiles_dev[1];
-            if (first && a.yclaim) {
+            if (first && a.wclaim) {
                 unsigned sm;
                 asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
                 if (sm < (unsigned)kMaxSmIds) {
                     const unsigned long long j =
-                        (unsigned long long)atomicAdd(&a.ctr->sm_slot[sm], 1u) * (unsigned)a.nsm + sm;
-                    if (j < nf && atomicExch(&a.yclaim[j], ep) != ep) t = (int)j;
+                        (unsigned long long)atomicAdd(&a.ctr->sm_slot[a.which][sm], 1u) * (unsigned)a.nsm + sm;
+                    if (j < nf && atomicExch(&a.wclaim[j], ep) != ep) t = (int)j;
                 }
             }
             while (t < 0) {
                 const unsigned i = atomicAdd(&a.ctr->tile_ctr[a.which], 1u);
                 if (i >= nf + nb) break;
                 if (i >= nf) t = a.ntiles - 1 - (int)(i - nf);
-                else if (!a.yclaim || atomicExch(&a.yclaim[i], ep) != ep) t = (int)i;
+                else if (!a.wclaim || atomicExch(&a.wclaim[i], ep) != ep) t = (int)i;
             }
         } else {
             const unsigned i = atomicAdd(&a.ctr->tile_ctr[a.which], 1u);
@@ -360,7 +360,8 @@ __device__ __forceinline__ void finish_tile(const SweepArgs<T>& a, int t, int gr
         const unsigned m = __reduce_max_sync(0xffffffffu, sbits);
         if (lane == 0) {
             a.tile_smax[t] = m;
-            if (m) atomicMax(&a.run[grid].smax32, m);
+            // (the maximum only grows: most tiles skip the atomic)
+            if (m && m > __ldcg(&a.run[grid].smax32)) atomicMax(&a.run[grid].smax32, m);
         }
     }
     if (WHICH == 1 && sizeof(T) == 4) {
@@ -369,7 +370,8 @@ __device__ __forceinline__ void finish_tile(const SweepArgs<T>& a, int t, int gr
             const double v = __shfl_xor_sync(0xffffffffu, m, o);
             m = (v <= m) ? m : v;
         }
-        if (lane == 0) atomicMax(&a.run[grid].wmax[acc], (unsigned long long)__double_as_longlong(m));
+        const unsigned long long mb = (unsigned long long)__double_as_longlong(m);
+        if (lane == 0 && mb > __ldcg(&a.run[grid].wmax[acc])) atomicMax(&a.run[grid].wmax[acc], mb);
     }
 }
 
@@ -497,12 +499,16 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
 
     const Consts<T>& K = a.K;
     const unsigned acc = a.ctr->acc;
-    // FP64 y: every tile records its estimated work for the adaptive y tiles
-    constexpr bool kRecord = (VAR == VAR_F64) && (LD == DIR_Y);
+    // FP64: every tile records its estimated work for the adaptive tiles
+    constexpr bool kRecord = (VAR == VAR_F64);
     unsigned kbad = 0, nfb = 0;
     bool aborted = false;
     // step count of this sweep: the claim word of the adaptive tiles
-    const unsigned long long ep = a.yclaim ? __ldcg(&a.ctr->steps) : 0ull;
+    const unsigned long long ep = a.wclaim ? __ldcg(&a.ctr->steps) : 0ull;
+    // recorded work of this warp's tiles (lane 0), added to the sweep's
+    // totals once at the end (an atomic per tile on one address serialises)
+    unsigned long long wsum = 0ull;
+    unsigned wbig = 0u;
     bool first = true;
 
     for (;;) {
@@ -720,20 +726,20 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
         // the tile's work is that of its busiest lane (one reduction per
         // tile: a reduction per row measured 13 % more FP64 instructions)
         if (kRecord) tcost = __reduce_max_sync(0xffffffffu, tcost);
-        if (kRecord && a.ycost && lane == 0) {
+        if (kRecord && a.wcost && lane == 0) {
             // the tile's work, spread evenly over its cost blocks (the tile
             // and grid fields are read again here rather than kept in
             // registers through the walk)
             const int4 tt = __ldcg(reinterpret_cast<const int4*>(a.tiles + t));  // grid, line0, cell0, ncell
-            const long long yblk = __ldcg(&a.grids[tt.x].yblk);
-            const int nrb = __ldcg(&a.grids[tt.x].nrb);
-            const int b0 = tt.z / kYBlock, b1 = (tt.z + tt.w - 1) / kYBlock;
+            const long long wblk = __ldcg(&a.grids[tt.x].wblk[LD]);
+            const int wnb = __ldcg(&a.grids[tt.x].wnb[LD]);
+            constexpr int B = walk_block(LD);
+            const int b0 = tt.z / B, b1 = (tt.z + tt.w - 1) / B;
             const float dens = (float)tcost / (float)(b1 - b0 + 1);
-            float* cst = a.ycost + yblk + (long long)(tt.y / kWarpLines) * nrb;
+            float* cst = a.wcost + wblk + (long long)(tt.y / kWarpLines) * wnb;
             for (int b = b0; b <= b1; ++b) cst[b] = dens;
-            const unsigned par = (unsigned)(__ldcg(&a.ctr->steps) & 1ull);
-            atomicAdd(&a.ctr->ycost_total[par], (unsigned long long)tcost);
-            atomicMax(&a.ctr->ycost_max[par], tcost);
+            wsum += tcost;
+            wbig = tcost > wbig ? tcost : wbig;
         }
         finish_tile<T, VAR, WHICH>(a, t, tile.grid, acc, redo && valid, tbad, smax, sbits, kbad, lane);
     }
@@ -744,6 +750,11 @@ __global__ void __launch_bounds__(kSweepThreads, (MinBlocks<T, VAR, LD>::value))
     }
     if constexpr (kStage) {
         if (lane == 0) bulk_wait<0>();  // this warp's stores have completed
+    }
+    if (kRecord && a.wcost && lane == 0 && wsum) {
+        const unsigned par = (unsigned)(__ldcg(&a.ctr->steps) & 1ull);
+        atomicAdd(&a.ctr->wcost_total[LD][par], wsum);
+        atomicMax(&a.ctr->wcost_max[LD][par], wbig);
     }
     for (int o = 16; o > 0; o >>= 1) {
         nfb += __shfl_xor_sync(0xffffffffu, nfb, o);

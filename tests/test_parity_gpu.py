@@ -189,24 +189,26 @@ def test_results_identical_for_every_tile_shape_schedule_and_graph(precision):
         assert np.array_equal(got, ref), (tl, cps, gs, sl)
 
 
-def test_adaptive_y_tiles_match_static_tiles_on_a_growing_blast():
-    """FP64 y tiles are re-cut every step from the recorded cost of the
-    previous y sweep; on a blast the cost varies strongly across the grid.
-    Whatever the cut, the results equal those of fixed tilings bit for bit."""
+def test_adaptive_tiles_match_static_tiles_on_a_growing_blast():
+    """FP64 x and y walk tiles are re-cut every step from the recorded cost of
+    the previous sweep in their direction; on a blast the cost varies
+    strongly across the grid.  Whatever the cut, the results equal those of
+    fixed tilings bit for bit (tile_len fixes the y tiles, span_len the x
+    tiles)."""
     pb = pr.sedov(200, 179)
     ada, _, _ = gpu_run(pb, 60, precision=64,
                         tuning=dict(tile_len=0, ctas_per_sm=0, graph_steps=20, span_len=0), record=False)
-    for tl in (8, 36, 256):
+    for tl, sl in ((8, 0), (36, 0), (256, 0), (0, 60), (0, 240), (36, 120)):
         got, _, _ = gpu_run(pb, 60, precision=64,
-                            tuning=dict(tile_len=tl, ctas_per_sm=0, graph_steps=0, span_len=0), record=False)
-        assert np.array_equal(got, ada), tl
+                            tuning=dict(tile_len=tl, ctas_per_sm=0, graph_steps=0, span_len=sl), record=False)
+        assert np.array_equal(got, ada), (tl, sl)
 
 
-@pytest.mark.parametrize("precision,per_step", [(64, 5), (32, 5)])
+@pytest.mark.parametrize("precision,per_step", [(64, 6), (32, 5)])
 def test_kernel_launch_count_reported(precision, per_step):
     """hydro_stats counts the kernels the step calls launch (bench.py reports
-    it as gpu_launches): FP64 prologue, y tiler, two sweeps, the CFL pass;
-    FP32 prologue and two sweeps of two passes each."""
+    it as gpu_launches): FP64 prologue, x and y tilers, two sweeps, the CFL
+    pass; FP32 prologue and two sweeps of two passes each."""
     pb = pr.sedov(64, 48)
     with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=precision) as c:
         c.set_state(0, pb.U)
