@@ -364,8 +364,13 @@ def roofline_for(workload: str, prec: int, cells: int, m: dict, fused: bool = Fa
         if alu:
             roof["alu_view"] = alu
     roof["traffic"] = prof.get("dram_bytes_per_sweep")
-    roof.update({"kernel": ("fused_step_kernel (with its second pass)" if fused
-                            else "sweep_x_kernel / sweep_y_kernel (mean of both)"),
+    if fused:
+        kname = "fused_step_kernel (with its second pass)"
+    elif prec == 64:
+        kname = "sweep_walk_kernel, x and y walks (mean of both)"
+    else:
+        kname = "sweep_x_kernel (x segments) / sweep_walk_kernel (y walk), mean of both"
+    roof.update({"kernel": kname,
                  "launch_ms": sweep_ms, "algorithmic_bytes_per_launch": alg_bytes})
     return roof
 

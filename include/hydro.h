@@ -130,17 +130,18 @@ typedef struct {
  *                 bit for bit; tile_len and span_len do not apply.
  * tile_len = 0 (default) and span_len = 0 take the tile length with the
  * best makespan of a list-scheduling model of the tile queue on the
- * resident warps (uniform cost per cell).  In FP64 contexts tile_len = 0
- * also makes the y tiles adaptive: every y sweep records an estimate of the
- * work (Newton iterations, powers, copies of uniform rows) spent on each row
- * of each 32-column group, and before the next y sweep the library splits each
- * model tile into pieces whose recorded work stays below the mean work
- * of a model tile (pieces reaching half that work and half the largest
- * piece of the previous y sweep are queued first, spread over the SMs), so
- * regions where the Riemann solver works harder get shorter tiles.  The
- * tiling follows the state, not the timing.  Results
- * are bit-identical for every admissible setting (a cell's update does not
- * depend on the schedule). */
+ * resident warps (uniform cost per cell).  In FP64 contexts they also make
+ * the tiles of their direction adaptive (tile_len: y, span_len: x): every
+ * sweep records an estimate of the work (Newton iterations, powers, copies
+ * of uniform cells) spent on each tile, spread over its cost blocks (a row
+ * of a 32-column group in y, 4 columns of a 32-row group in x), and before
+ * the next sweep in that direction the library splits each model tile into
+ * pieces whose recorded work stays below the mean work of a model tile
+ * (pieces reaching half that work and half the largest piece of the
+ * previous sweep are queued first, spread over the SMs), so regions where
+ * the Riemann solver works harder get shorter tiles.  The tiling follows
+ * the state, not the timing.  Results are bit-identical for every
+ * admissible setting (a cell's update does not depend on the schedule). */
 typedef struct {
     int tile_len;
     int ctas_per_sm;
