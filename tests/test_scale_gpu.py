@@ -6,7 +6,11 @@ benchmark times (model-default tiles, CUDA graph of 20 steps):
   against a single-grid run bit for bit, and FP32 against FP64 on the same
   dt sequence at a stated density error;
 * the paper's 10000^2 point explosion, 10 steps: every cell beyond the
-  blast's reach exactly ambient, the corner against an oracle window.
+  blast's reach exactly ambient, the corner against an oracle window;
+* the 8192^2 periodic random-mode field (the benchmark's default), FP64 and
+  FP32, and the 16384^2 periodic Kelvin-Helmholtz layer (FP32): seeded
+  windows of the full-size result against the oracle run on the same windows
+  of the initial field with the GPU's dt sequence.
 """
 import numpy as np
 import pytest
@@ -107,3 +111,73 @@ def test_explosion_10000_sampled_against_oracle_window():
     np.testing.assert_allclose(gdts, odts, rtol=1e-12)
     m = 256 - reach
     assert rel_err(got[:, :m, :m], want[:, :m, :m]) <= TOL64
+
+
+def _periodic_window(U, x0, y0, w, m):
+    """The (w + 2m)^2 block of a periodic field around the w x w window at
+    (x0, y0), wrapped across the edges."""
+    ny, nx = U.shape[1], U.shape[2]
+    iy = np.arange(y0 - m, y0 + w + m) % ny
+    ix = np.arange(x0 - m, x0 + w + m) % nx
+    return np.ascontiguousarray(U[:, iy][:, :, ix])
+
+
+def _windows_against_oracle(pb, got, dts, k, w, corners):
+    """For each window corner: the oracle advances the window of the initial
+    field with a margin of 2k + 1 cells (its transmissive edges disturb at most
+    two cells per sweep, 2k cells in k steps) by the given dt sequence; returns
+    the GPU's window and the oracle's, margins cut off."""
+    m = 2 * k + 1
+    out = []
+    for x0, y0 in corners:
+        win = _periodic_window(pb.U, x0, y0, w, m)
+        want, _, _ = O.run(win, pb.h, (pr.TRANSMISSIVE,) * 4, k, dt_override=dts, threads=0)
+        mine = _periodic_window(got, x0, y0, w, 0)
+        out.append((mine, want[:, m:m + w, m:m + w]))
+    return out
+
+
+def _corners(n, w, seed, count=3):
+    rng = np.random.default_rng(seed)
+    # one window across the periodic corner, the others anywhere
+    return [(n - w // 2, n - w // 2)] + [tuple(int(v) for v in rng.integers(0, n, 2)) for _ in range(count - 1)]
+
+
+def test_random_modes_8192_fp64_and_fp32_windows_against_oracle():
+    """The benchmark's default field at full size (8192^2, periodic), 6 steps in
+    the benchmark's launch configuration: FP64 windows equal the oracle's to
+    1e-11; FP32 on the FP64 dt sequence is within the stated L1 density error
+    of the FP64 oracle on the same windows."""
+    k, w = 6, 128
+    pb = pr.random_modes(8192)
+    with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=64) as c:
+        c.set_state(0, pb.U)
+        gdts = c.step(k, record_dt=True)
+        got64 = c.get_state(0)
+    with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=32) as c:
+        c.set_state(0, pb.U)
+        c.step(k, dt_override=gdts)
+        got32 = c.get_state(0)
+    corners = _corners(8192, w, seed=8192)
+    for mine, want in _windows_against_oracle(pb, got64, gdts[:, 0], k, w, corners):
+        assert rel_err(mine, want) <= TOL64
+    for mine, want in _windows_against_oracle(pb, got32, gdts[:, 0], k, w, corners):
+        l1 = float(np.abs(mine[0] - want[0]).sum() / np.abs(want[0]).sum())
+        assert l1 <= TOL_L1_FP32_BATCH, l1
+
+
+def test_kelvin_helmholtz_16384_fp32_windows_against_oracle():
+    """The large FP32 run at full size (16384^2 periodic shear layer), 4 steps:
+    windows (one across the periodic corner, one on the shear layer) within
+    the stated L1 density error of the FP64 oracle run on the same windows with
+    the GPU's own dt sequence."""
+    k, w = 4, 128
+    pb = pr.kelvin_helmholtz(16384)
+    with H.Context([(pb.nx, pb.ny, pb.h, pb.bc)], precision=32) as c:
+        c.set_state(0, pb.U)
+        dts = c.step(k, record_dt=True)
+        got = c.get_state(0)
+    corners = _corners(16384, w, seed=16384, count=2) + [(5000, 16384 // 4 - w // 2)]
+    for mine, want in _windows_against_oracle(pb, got, dts[:, 0], k, w, corners):
+        l1 = float(np.abs(mine[0] - want[0]).sum() / np.abs(want[0]).sum())
+        assert l1 <= TOL_L1_FP32_BATCH, l1
