@@ -131,6 +131,12 @@ __device__ __forceinline__ bool below_floor(double x, double c) {
            (ic != 0 || ix != (long long)0x8000000000000000ull);
 }
 __device__ __forceinline__ bool below_floor(float x, float c) { return x < c; }
+// x raised to the floor c.  FP64: x < c selects c (a NaN x stays NaN).
+// FP32 (bound by instruction issue): one max instruction, which returns c
+// for a NaN x -- a NaN state is still reported through its own cell's
+// update, which reads the conserved state itself.
+__device__ __forceinline__ double floor_at(double x, double c) { return below_floor(x, c) ? c : x; }
+__device__ __forceinline__ float floor_at(float x, float c) { return fmaxf(x, c); }
 // 0 <= x and x < 0 exactly as the IEEE comparisons (a NaN is neither), on
 // the bit pattern: the sign bit, with -0 counted as zero
 __device__ __forceinline__ bool ge_zero(double x) {
@@ -219,14 +225,14 @@ __device__ __forceinline__ T pow_z(const Consts<T>& K, T p, T pK, T ip) {
 template <class T>
 __device__ __forceinline__ Prim<T> cons_to_prim(const Consts<T>& K, const Cons<T>& U, T& ir) {
     Prim<T> W;
-    W.r = below_floor(U.r, K.rho_floor) ? K.rho_floor : U.r;
+    W.r = floor_at(U.r, K.rho_floor);
     ir = trcp(W.r);
     W.u = U.mn * ir;
     W.v = U.mt * ir;
     // p = (g-1) E - (g-1)/2 rho |u|^2, with rho |u|^2 = m_n u_n + m_t u_t
     T p = tfma(-K.G7, tfma(U.mn, W.u, U.mt * W.v), K.gm1 * U.E);
     const T pm = W.r * K.cf2g;
-    W.p = below_floor(p, pm) ? pm : p;
+    W.p = floor_at(p, pm);
     return W;
 }
 
@@ -262,10 +268,10 @@ __device__ __forceinline__ double minmod(double a, double b) {
     const long long m = (long long)(ma < mb ? ma : mb) | (ia & (long long)0x8000000000000000ull);
     return take ? __longlong_as_double(m) : 0.0;
 }
-// FP32: the sign test through the product (0 when it underflows, i.e. both
-// slopes below ~1e-19 in magnitude), then the argument of smaller magnitude.
+// FP32: minmod(a, b) is the median of a, b and 0 -- four min/max
+// instructions, exactly a, b or a zero, with no product to underflow.
 __device__ __forceinline__ float minmod(float a, float b) {
-    return (a * b > 0.0f) ? ((fabsf(a) < fabsf(b)) ? a : b) : 0.0f;
+    return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));
 }
 
 // Monotonized central slope: 0 unless a and b are both > 0 or both < 0,
@@ -343,15 +349,13 @@ __device__ __forceinline__ bool same_bits(const Prim<T>& a, const Prim<T>& b) {
     return diff_bits(a, b) == 0;
 }
 
-// x > 0 for x not NaN (positive finite or +inf), tested on the bit pattern.
+// x > 0 for x not NaN (positive finite or +inf); FP64 on the bit pattern
+// (integer pipe), FP32 by one compare.
 __device__ __forceinline__ bool positive(double x) {
     const long long i = __double_as_longlong(x);
     return i > 0 && i <= 0x7ff0000000000000ll;
 }
-__device__ __forceinline__ bool positive(float x) {
-    const int i = __float_as_int(x);
-    return i > 0 && i <= 0x7f800000;
-}
+__device__ __forceinline__ bool positive(float x) { return x > 0.0f; }  // one compare; NaN fails
 
 // Characteristic tracing (the trace variant) of the cell W0 with limited
 // slopes D: the slopes split into the waves of the primitive Jacobian
@@ -387,11 +391,11 @@ __device__ __forceinline__ void characteristic_trace(const Consts<T>& K, T hdtdx
     wave(W0.u, a2, T(1), T(0), T(0), T(0));
     wave(W0.u, Dv, T(0), T(0), T(1), T(0));
     wave(W0.u + c, a4, T(1), cr, T(0), c2);
-    WL.r = below_floor(WL.r, K.rho_floor) ? K.rho_floor : WL.r;
-    WR.r = below_floor(WR.r, K.rho_floor) ? K.rho_floor : WR.r;
+    WL.r = floor_at(WL.r, K.rho_floor);
+    WR.r = floor_at(WR.r, K.rho_floor);
     const T pml = WL.r * K.cf2g, pmr = WR.r * K.cf2g;
-    WL.p = below_floor(WL.p, pml) ? pml : WL.p;
-    WR.p = below_floor(WR.p, pmr) ? pmr : WR.p;
+    WL.p = floor_at(WL.p, pml);
+    WR.p = floor_at(WR.p, pmr);
 }
 
 // Differences of primitive states, a - b.
@@ -469,11 +473,11 @@ __device__ __forceinline__ void trace(const Consts<T>& K, T hdtdx /* -dt/(2dx) *
     WR.u = tfma(T(0.5), Du, cu);
     WR.v = tfma(T(0.5), Dv, cv);
     WR.p = tfma(T(0.5), Dp, cp);
-    WL.r = below_floor(WL.r, K.rho_floor) ? K.rho_floor : WL.r;
-    WR.r = below_floor(WR.r, K.rho_floor) ? K.rho_floor : WR.r;
+    WL.r = floor_at(WL.r, K.rho_floor);
+    WR.r = floor_at(WR.r, K.rho_floor);
     const T pml = WL.r * K.cf2g, pmr = WR.r * K.cf2g;
-    WL.p = below_floor(WL.p, pml) ? pml : WL.p;
-    WR.p = below_floor(WR.p, pmr) ? pmr : WR.p;
+    WL.p = floor_at(WL.p, pml);
+    WR.p = floor_at(WR.p, pmr);
 }
 
 // ------------------------------------------------------ Riemann solver --
