@@ -252,6 +252,7 @@ __device__ __forceinline__ T cfl_speed(const Consts<T>& K, const Cons<T>& U) {
     T c;
     if (sizeof(T) == 8) c = K.sqg * w.p * trsqrt(w.r * w.p);
     else c = tsqrt(K.gamma * w.p * ir);
+    if constexpr (sizeof(T) == 4) return fmaxf(au, av) + c;  // one instruction
     return ((au > av) ? au : av) + c;
 }
 

@@ -128,8 +128,7 @@ struct FluxOp<double, VAR_F64, SV> {
 // p* < 1e-3 min(pL,pR) (strong double rarefaction).
 __device__ __forceinline__ bool near_vacuum_f32(const Prim<float>& L, const Prim<float>& R,
                                                 const Star<float>& s) {
-    const float pmn = (L.p < R.p) ? L.p : R.p;
-    const float pmx = (L.p < R.p) ? R.p : L.p;
+    const float pmn = fminf(L.p, R.p), pmx = fmaxf(L.p, R.p);
     return pmn < 1e-6f * pmx || s.floored || s.p < 1e-3f * pmn;
 }
 
