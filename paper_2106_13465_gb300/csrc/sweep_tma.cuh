@@ -4,32 +4,40 @@
 //
 // Work decomposition.  A persistent grid of CTAs whose warps claim tasks from
 // a work counter, so one launch covers any number of grids of any shapes.
-//   x sweep: a task is a run of overlapping 64-cell segments of one row
-//            (segment k starts at x = -4 + 60 k); lane l holds cells 2l and
-//            2l+1 of the segment and takes its neighbours' primitives, faces
-//            and fluxes by warp shuffles; lanes 1..30 hold the 60 results.
-//   y sweep: a task (tile) is 32 columns x L rows; lane l walks column
-//            line0 + l from row cell0 - 2 to cell0 + L + 1 (the 5-point
-//            stencil of Figs. 1-2) with a 2-cell window of conserved and
-//            primitive states, the right face of the previous cell and the
-//            flux at the previous interface in registers.
-// In both, every interface is solved once per task and every cell written
+//   x sweep, FP32 (sweep_x_kernel): a task is a run of overlapping 64-cell
+//            segments of one row (segment k starts at x = -4 + 60 k); lane l
+//            holds cells 2l and 2l+1 of the segment and takes its
+//            neighbours' primitives, faces and fluxes by warp shuffles;
+//            lanes 1..30 hold the 60 results.
+//   line walks (sweep_walk_kernel): a task (tile) is 32 lines x L cells;
+//            lane l walks line line0 + l from cell0 - 2 to cell0 + L + 1 (the
+//            5-point stencil of Figs. 1-2) with a window of the last two
+//            conserved states, the last primitives and their one-sided
+//            difference, the right face of the previous cell and the flux
+//            at the previous interface in registers.  y sweep (both
+//            precisions): the lines are columns.  x sweep (FP64): the lines
+//            are rows.  FP64 tiles are cut every step from the work the
+//            previous sweep in their direction recorded (adaptive tiles).
+// In all, every interface is solved once per task and every cell written
 // once.
 //
 // Data movement.  Each warp owns a ring of shared-memory slots fed by TMA
 // (cp.async.bulk.tensor, one elected lane, completion on an mbarrier per
-// slot).  x: a slot holds one segment (64 cells x 4 planes); lane l reads its
-// two cells with one 8- or 16-byte load per plane, and the warp writes its 60
-// results as consecutive cells of each plane.  y: a slot holds 4 rows x 32
-// columns x 4 planes; lane l reads column l (consecutive words) and a warp
-// writes 32 consecutive cells per plane.  The ring is refilled as slots are
-// consumed, so several are in flight while the warp computes.
+// slot).  x segments: a slot holds one segment (64 cells x 4 planes); lane l
+// reads its two cells with one 8- or 16-byte load per plane, and the warp
+// writes its 60 results as consecutive cells of each plane.  y walk: a slot
+// holds 4 rows x 32 columns x 4 planes; lane l reads column l (consecutive
+// words) and a warp writes 32 consecutive cells per plane.  x walk: a slot
+// holds 4 columns x 32 rows x 4 planes; the warp collects its outputs in a
+// staging block of the same shape and writes it by a TMA store.  The ring is
+// refilled as slots are consumed, so several are in flight while the warp
+// computes.
 //
 // Boundary conditions are folded into the read: a position k outside [0, n)
 // of a line takes the mirror cell (reflective: normal momentum negated;
 // transmissive) or the wrap-around cell (periodic).  Mirror cells come by
-// shuffle from the same x segment, or from the first y chunk and the y
-// walker's register window; wrap-around cells with a direct load.  TMA reads
+// shuffle from the same x segment, or from a walk's first chunk and its
+// register window; wrap-around cells with a direct load.  TMA reads
 // outside the grid are zero-filled and feed no result.
 //
 // Every wait on an mbarrier is bounded: after SweepArgs::wait_limit polls
