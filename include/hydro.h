@@ -158,8 +158,8 @@ typedef struct {
  *                  error, a tile outside its grid was skipped (sticky until
  *                  hydro_set_state)
  *   kernel_launches  kernels the step calls launched (host count; a step of
- *                  an FP64 context launches 5 with adaptive y tiles, of an
- *                  FP32 context 5; a fused step 3)
+ *                  an FP64 context launches 6 with adaptive x and y tiles, of
+ *                  an FP32 context 5; a fused step 3)
  *   wait_site, wait_tile  the first bounded wait that gave up since the last
  *                  hydro_set_state: kernel (0 none, 1 x sweep, 2 y sweep,
  *                  3 fused step, 4 its FP32 second pass) and work-list tile */

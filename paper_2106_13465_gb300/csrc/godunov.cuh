@@ -698,7 +698,7 @@ __device__ __forceinline__ T sound_speed(const Consts<T>& K, const Prim<T>& W) {
 constexpr unsigned kEqualStateWork = 40u;
 
 // A rough count of the FP64 operations of a cell and its interface solve,
-// used only to schedule work (adaptive y tiles): a fixed part (conversion,
+// used only to schedule work (adaptive tiles): a fixed part (conversion,
 // trace, update, sides, guess, sampling, flux), and per evaluation of the
 // pressure functions the Newton update and both sides, where a rarefaction
 // power far from p_K (exp2/log2) costs about four times the series near it.

@@ -564,8 +564,8 @@ cudaError_t enqueue_step_t(hydro_ctx* c, int parity, const double* ovr, double* 
     return cudaSuccess;
 }
 
-// Kernels one step launches (enqueue_step_t): the dt prologue, the y tiler
-// (adaptive y tiles), and per sweep the sweep kernel plus, FP64, the CFL
+// Kernels one step launches (enqueue_step_t): the dt prologue, a tiler per
+// direction with adaptive tiles, and per sweep the sweep kernel plus, FP64, the CFL
 // pass after the second sweep or, FP32, the near-vacuum second pass.  A
 // fused step: the prologue, the step kernel and the CFL or second pass.
 int launches_per_step(const hydro_ctx* c) {

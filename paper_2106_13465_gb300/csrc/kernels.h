@@ -30,15 +30,18 @@
 // column), the second writes the tile's cells to the other state buffer.
 // Stored as (grid, line0 = k, cell0 = y0, ncell = rows).
 //
-// Work lists.  y sweep: a tile is 32 columns (one per lane) x ncell rows.
-// x sweep: a tile is a run of consecutive segments of one row, stored as
-// (grid, line0 = row, cell0 = first segment index, ncell = segments).
+// Work lists.  Walks (y sweep; FP64 x sweep): a tile is 32 lines (one per
+// lane: columns in y, rows in x) x ncell cells.  FP32 x sweep: a tile is a
+// run of consecutive segments of one row, stored as (grid, line0 = row,
+// cell0 = first segment index, ncell = segments).
 //
-// Adaptive y tiles (FP64).  The rows of each column group (32 columns) are
-// divided into blocks of kYBlock rows.  Every y sweep records, per block, the
-// estimated work of the tile that covered it (per row, the largest solve_work
-// over the warp's lanes, spread evenly over the tile's blocks); before the
-// next y sweep a small kernel splits each tile of a static tiling (the one
+// Adaptive walk tiles (FP64, both directions).  The cells of each line group
+// (32 lines) are divided into cost blocks of walk_block(d) cells (1 row in y,
+// 4 columns in x, so that x pieces keep their 32-byte alignment).  Every walk
+// records, per block, the estimated work of the tile that covered it (the
+// largest over the warp's lanes of the sum of solve_work over the lane's
+// cells, spread evenly over the tile's blocks); before the next sweep in the
+// same direction a small kernel splits each tile of a static tiling (the one
 // the scheduling model picks for uniform cost, in whole blocks) into pieces
 // whose recorded work stays below kYCostCap times the mean work of a static
 // tile.  Uniform work keeps the static tiles; where the Riemann solver works
@@ -46,7 +49,7 @@
 // average when the queue runs dry.  Long pieces are queued before the others
 // (longest jobs first, the short ones fill the tail): those of at least
 // kYBigJob times the mean and kYBigOfMax times the largest piece of the
-// previous y sweep.  Where a few rows hold hard Riemann problems (one-row
+// previous sweep.  Where a few lines hold hard Riemann problems (one-block
 // pieces at several times the mean) only they count as long, so they start
 // at once, spread over the SMs, and do not wait behind the ordinary tiles;
 // where the work is spread evenly the ordinary tiles are the long jobs and
