@@ -1,5 +1,7 @@
 """Host logic of bench.py that needs no GPU: the hash tying the committed ncu
-figures (profiles/traffic.json) to the kernel sources they were taken on."""
+figures (profiles/traffic.json) to the kernel sources they were taken on, the
+roofline views built from them, and the clock record (median SM clock under
+load, throttle reasons) that decides whether a bench line stands."""
 import importlib.util
 import os
 
@@ -32,3 +34,80 @@ def test_hash_ignores_comments_and_layout_but_not_code():
     assert b.strip_comments(base) == b.strip_comments(same)
     assert b.strip_comments(base) != b.strip_comments(other)
 
+
+
+def test_roofline_views_from_recorded_figures(monkeypatch):
+    b = _bench()
+    cells = 8192 * 8192
+    rec = {"source_hash": "h", "dram_bytes_per_sweep": 4.9e9, "fp64_flops_per_cell_sweep": 216.0}
+    monkeypatch.setattr(b, "recorded_profile", lambda key: dict(rec) if key == "modes8192_fp64" else {})
+    monkeypatch.setattr(b, "load_peaks", lambda: {"hbm_gbs": 6788.3})
+    # FP64: the FP64-pipe view (216 flops per cell-sweep) outweighs the HBM view
+    r = b.roofline_for("modes8192_fp64", 64, cells, {"sweep_ms": 20.0})
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 216.0 * cells / 20e-3 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / b.FP64_PEAK_TFLOPS) < 1e-12
+    assert abs(r["hbm_view"]["achieved"] - 2 * 4 * 8 * cells / 20e-3 / 1e9) < 1e-6
+    assert r["traffic"] == 4.9e9 and r["algorithmic_bytes_per_launch"] == 2 * 4 * 8 * cells
+    # a fused launch does both sweeps: twice the flops and the step kernel's time
+    f = b.roofline_for("modes8192_fp64", 64, cells, {"step_kernels_ms": 40.0}, fused=True)
+    assert f["traffic"] is None and f["bound"] == "hbm"  # no recorded figures for the fused key
+    # FP32: the HBM view with the measured peak; no recorded traffic -> null
+    r = b.roofline_for("modes8192_fp32", 32, cells, {"sweep_ms": 0.8})
+    assert r["bound"] == "hbm" and r["peak"] == 6788.3 and r["peak_source"] == "measured"
+    assert abs(r["achieved"] - 2 * 4 * 4 * cells / 0.8e-3 / 1e9) < 1e-6
+    assert r["traffic"] is None
+    # without the measured peaks: the fallback, said so
+    monkeypatch.setattr(b, "load_peaks", lambda: {})
+    r = b.roofline_for("modes8192_fp32", 32, cells, {"sweep_ms": 0.8})
+    assert r["peak"] == 6800.0 and r["peak_source"] == "fallback"
+
+
+def test_recorded_figures_only_for_the_current_sources(monkeypatch):
+    b = _bench()
+    import json
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        rec = json.load(fh)
+    key = next(k for k in rec if not k.startswith("_"))
+    monkeypatch.setattr(b, "kernel_source_hash", lambda: rec[key]["source_hash"])
+    assert b.recorded_profile(key)["dram_bytes_per_sweep"] == rec[key]["dram_bytes_per_sweep"]
+    monkeypatch.setattr(b, "kernel_source_hash", lambda: "0000000000000000")
+    assert b.recorded_profile(key) == {}
+    assert b.recorded_profile("no_such_workload") == {}
+
+
+class _FakeProc:
+    def __init__(self, out):
+        self.out = out
+
+    def terminate(self):
+        pass
+
+    def kill(self):
+        pass
+
+    def communicate(self, timeout=None):
+        return self.out, ""
+
+
+def test_clock_sampler_median_under_load_and_reasons(monkeypatch):
+    b = _bench()
+    monkeypatch.setattr(b.time, "sleep", lambda s: None)
+    # index, sm, max sm, power, active mask, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    rows = ["0, 345, 2070, 150.0, 0x0, Not Active, Not Active, Not Active, Not Active",  # idle
+            "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, [N/A], 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage line"]
+    s = b.ClockSampler(None)
+    s.proc = _FakeProc("\n".join(rows) + "\n")
+    c = s.stop()
+    assert c["samples"] == 5                       # the malformed line is skipped
+    assert c["sm_mhz"] == 2070.0                   # median of the loaded samples (idle one left out)
+    assert c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    s = b.ClockSampler(None)
+    s.proc = _FakeProc("0, 1200, 2070, 900.0, 0x8, Active, Not Active, Active, Not Active\n")
+    assert b.ClockSampler.stop(s)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert b.ClockSampler(None).stop() is None     # no nvidia-smi: no clock record
