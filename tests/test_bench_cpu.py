@@ -111,3 +111,38 @@ def test_clock_sampler_median_under_load_and_reasons(monkeypatch):
     s.proc = _FakeProc("0, 1200, 2070, 900.0, 0x8, Active, Not Active, Active, Not Active\n")
     assert b.ClockSampler.stop(s)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     assert b.ClockSampler(None).stop() is None     # no nvidia-smi: no clock record
+
+
+def _run_bench(args, env_extra=None):
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """The reference arm (the oracle on the host cores) runs without a GPU and
+    prints one JSON line with the contract's keys; under torchrun only rank 0
+    prints; fewer than 3 warm-up steps are refused."""
+    import json
+    p = _run_bench(["--impl", "reference", "--workload", "sedov128_fp64", "--steps", "2", "--warmup", "3"])
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [l for l in p.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["dtype"] == "f64"
+    assert d["config"]["workload"] == "sedov128_fp64"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    p = _run_bench(["--impl", "reference", "--workload", "sedov128_fp64", "--steps", "1", "--warmup", "3",
+                    "--gpus", "2"], {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert p.returncode == 0 and p.stdout.strip() == ""
+    p = _run_bench(["--impl", "reference", "--workload", "sedov128_fp64", "--steps", "1", "--warmup", "2"])
+    assert p.returncode != 0 and "--warmup must be >= 3" in p.stderr
