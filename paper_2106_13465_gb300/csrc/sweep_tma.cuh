@@ -244,7 +244,7 @@ struct WarpRing {
         tma_load_3d(base + s * SLOT, map, x, y, 0, &bar[s]);
         pending |= 1u << s;
     }
-    // all lanes: wait for slot s, at most `limit` polls (the verdict is
+    // all lanes: wait for slot s, at most `limit` polls (the outcome is
     // warp-uniform)
     __device__ __forceinline__ bool wait(int s, int lane, unsigned limit) {
         const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[s], (parity >> s) & 1u, limit));
