@@ -78,7 +78,7 @@ template <class T> struct Cons { T r, mn, mt, E; };   // (rho, m_n, m_t, E)
 // a step that reached the pressure floor (an interface the FP64
 // near-vacuum pass redoes) -- stay far inside that range for pressures and speeds well
 // inside the FP32 range.  Measured on the 8192^2 random-mode field: the
-// same results, FP32 sweeps 2.6 % faster.
+// same 200-step L1 density error to all digits, FP32 sweeps 2.6 % faster.
 // FP64 powers through exp2(e log2 x): within a few ulp, and cheaper on the
 // FP64 pipe than the extra-precise pow
 __device__ __forceinline__ double tpow(double x, double e) { return exp2(e * log2(x)); }
